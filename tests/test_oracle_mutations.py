@@ -1,0 +1,50 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of ``oracle/sem_oracle.c`` (on the CPU,
+in a temporary directory), builds it, and runs the pin suite against it with
+``SEM_ORACLE_LIB`` pointing at the broken library.  The suite must fail.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sem_oracle.c")
+
+MUTATIONS = {
+    "transposed_D_in_second_stage": ("acc += D[m * n + i] * wr", "acc += D[i * n + m] * wr"),
+    "dropped_cross_term": ("wr[q] = g[0] * ur + g[1] * us + g[2] * ut;",
+                           "wr[q] = g[0] * ur + g[1] * us;"),
+    "cofactor_sign": ("cof[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];",
+                      "cof[0][1] = J[1][0] * J[2][2] - J[1][2] * J[2][0];"),
+    "wrong_lattice_index": ("gy = (long)ey * N + j", "gy = (long)ey * N + i"),
+    "gll_weight_formula": ("w[j] = 2.0 / (N * (N + 1.0) * P * P);",
+                           "w[j] = 2.0 / ((N + 1.0) * (N + 1.0) * P * P);"),
+    "D_corner_entry": ("v = N * (N + 1.0) / 4.0;", "v = N * (N + 1.0) / 2.0;"),
+    "cg_beta_inverted": ("double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    "gs_last_copy_wins": ("else sum[g] += u[l];", "else sum[g] = u[l];"),
+    "mask_misses_a_face": ("gz == 0 || gz == mz", "gz == 0"),
+    "geometry_weight_missing": ("double W = w[i] * w[j] * w[k];", "double W = w[i] * w[j];"),
+    "ut_wrong_stride": ("ut += D[k * n + m] * ue[i + n * (j + n * m)];",
+                        "ut += D[k * n + m] * ue[i + n * (m + n * j)];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    before, after = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(before) == 1, f"mutation anchor for {name} not found exactly once"
+    mutated = tmp_path / "sem_oracle_mut.c"
+    mutated.write_text(src.replace(before, after))
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
+                    str(mutated), "-o", str(lib), "-lm"], check=True)
+    env = dict(os.environ, SEM_ORACLE_LIB=str(lib))
+    proc = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert proc.returncode != 0, f"pins did not catch mutation {name}:\n{proc.stdout[-2000:]}"
