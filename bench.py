@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Benchmark: conjugate-gradient throughput on the SEM Poisson operator.
+
+Workload (one "step" = one complete solve): a 32x32x32 box of hexahedra
+(E = 32768) of order N = 7, interior vertices jittered by +-5 % of the element
+size (seed 2), Dirichlet boundary, right-hand side b = mask(QQ^T f) with
+f ~ N(0, 1) per local node (seed 3, +rank for extra ranks), CG from x = 0 to
+sqrt(<r,r>/<b,b>) <= 1e-8.  Throughput is the paper's GDOFS
+(E N^3 iterations / time / 1e9, Section VIII-B).  Inputs already sit in HBM
+when the timed region starts; the geometric factors alone (805 MB) exceed the
+129 MB L2, so no flush is needed between steps.
+
+Also reported on the same JSON line:
+  e2e           the same metric through the public API with host buffers
+                (pinned b copied in and x copied out every step)
+  roofline      the dominant kernel (the fused CG operator kernel) timed with
+                CUDA events on libsem's stream, against the FP64 pipe peak
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
+  clocks        nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+Multi-GPU (torchrun): every rank solves an independent problem (replicas,
+no data-path collective); the value is the sum over ranks over the slowest
+rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG GDOF/s to 1e-8 rel. residual, mixed vs FP64 on GB300; serve p50/p99 ms"
+# FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock) = 1.259 TFLOP/s
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
+              for f in ("sem_ax.cu", "sem_device.cuh", "sem_internal.h")]
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--nx", type=int, default=32, help="elements per direction")
+    ap.add_argument("--N", type=int, default=7, help="polynomial order")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=100000)
+    ap.add_argument("--ax-reps", type=int, default=20, help="launches timed for the roofline")
+    ap.add_argument("--cpu-iters", type=int, default=10, help="oracle CG iterations per CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"fp64 CG to {a.tol:g} rel. residual, box {a.nx}x{a.nx}x{a.nx} (E={a.nx ** 3}), N={a.N}, "
+            f"jitter 5% seed 2, random-normal RHS seed 3")
+
+
+def config_of(a, world, iters=None):
+    c = {"workload": workload_name(a), "E": a.nx ** 3, "N": a.N, "tol": a.tol,
+         "local_dofs": a.nx ** 3 * (a.N + 1) ** 3, "gdofs_per_iter": a.nx ** 3 * a.N ** 3,
+         "l2": "inputs larger than L2 (805 MB of geometric factors per problem)",
+         "parallelism": f"replicas x{world} (independent problems, no collective)"}
+    if iters is not None:
+        c["cg_iters"] = iters
+    return c
+
+
+def ax_flops_per_elem(N):
+    q = N + 1
+    return 12 * q ** 4 + 15 * q ** 3
+
+
+def source_sha(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags) if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+# ------------------------------------------------------------------ oracle (CPU) timing
+def time_oracle(a, iters, steps=1):
+    """FP64 oracle CG on the full workload, `iters` iterations per step (set-up
+    excluded).  Returns (GDOF/s, seconds per step)."""
+    import oracle
+    from paper_2606_12650_gb300.inputs import box_vertices, normal_field
+    P = oracle.Problem(a.nx, a.nx, a.nx, a.N, box_vertices(a.nx, a.nx, a.nx, 0.05, seed=2))
+    b = P.mask(P.gs(normal_field(P.nL, 3)))
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        P.cg(b, maxit=iters, tol=0.0)
+        times.append(time.perf_counter() - t0)
+    return P.E * a.N ** 3 * iters / (sum(times) / len(times)) / 1e9, times
+
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    iters = a.cpu_iters
+    gdofs, times = time_oracle(a, iters, steps=a.warmup + a.steps)
+    timed = times[a.warmup:]
+    value = a.nx ** 3 * a.N ** 3 * iters * len(timed) / sum(timed) / 1e9
+    sample = (f"{iters} FP64 CG iterations per step on the full E={a.nx ** 3}, N={a.N} problem, "
+              f"single-threaded C oracle, set-up excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(timed) / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(a, 1),
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_12650_gb300 import Mesh, sem
+    from paper_2606_12650_gb300.inputs import box_vertices, normal_field
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sem.init([f"--device={local}"])
+    stream = sem.stream()
+    torch.cuda.set_stream(stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier(device_ids=[local])
+
+    nx, N = a.nx, a.N
+    E = nx ** 3
+    M = Mesh(nx, nx, nx, N, box_vertices(nx, nx, nx, 0.05, seed=2))
+    f = torch.from_numpy(normal_field(M.nL, 3 + rank)).cuda()
+    b = f.clone()
+    M.gs(b)
+    M.mask(b)
+    x = torch.empty_like(b)
+
+    for _ in range(a.warmup):
+        iters, rel = M.cg_solve(b, x, a.tol, a.maxit)
+
+    # ---- timed region: K complete solves, inputs resident in HBM
+    n_launch0 = sem.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters_total = 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(a.steps):
+            it, rel = M.cg_solve(b, x, a.tol, a.maxit)
+            iters_total += it
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = sem.launch_count() - n_launch0
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    dofs = float(E * N ** 3 * iters_total)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+        dofs = float(dd.item())
+    value = dofs / (t_max * 1e-3) / 1e9
+    true_res = M.true_res(b, x)
+
+    # ---- dominant kernel: the fused CG operator kernel, timed alone on libsem's stream
+    for _ in range(3):
+        sem.run("cg_ax", M.handle)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.ax_reps):
+        sem.run("cg_ax", M.handle)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ax_ms = e0.elapsed_time(e1) / a.ax_reps
+    flops = E * ax_flops_per_elem(N)
+    achieved = flops / (ax_ms * 1e-3) / 1e9
+    bytes_alg = E * (N + 1) ** 3 * 80  # r, p in; p, w out; 6 geometric factors (FP64)
+    fp64 = sem.OutDouble()
+    sem.run("peak_fma", 0, 4096, fp64)
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh).get("ax_f64_cg", {})
+        if t.get("source_sha") == source_sha(AX_SOURCES) and t.get("E") == E and t.get("N") == N:
+            traffic = t.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                "kernel": f"ax_f64_kernel<{N + 1},2,CG>", "launch_ms": ax_ms,
+                "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+                "hbm_gbs_at_alg_bytes": bytes_alg / (ax_ms * 1e-3) / 1e9,
+                "fp64_probe_gflops": fp64.value / 1e9,
+                "peak_note": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 2 DFMA/clk x "
+                             "2 flop x 2.07 GHz); fp64_probe_gflops is the same pipe measured live"}
+
+    # ---- end to end through the public API, host buffers
+    e2e = None
+    if not a.no_e2e:
+        bh = torch.empty(M.nL, dtype=torch.float64).pin_memory()
+        xh = torch.empty(M.nL, dtype=torch.float64).pin_memory()
+        bh.copy_(b.cpu())
+        sem.update(bh, sem.SEM_ALLOC)
+        sem.update(xh, sem.SEM_ALLOC)
+        sem.update(bh, sem.SEM_TO)
+        M.cg_solve(bh, xh, a.tol, a.maxit)
+        sem.update(xh, sem.SEM_FROM)
+        sem.sync()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e_iters = 0
+        for _ in range(a.steps):
+            sem.update(bh, sem.SEM_TO)
+            it, _ = M.cg_solve(bh, xh, a.tol, a.maxit)
+            sem.update(xh, sem.SEM_FROM)
+            sem.sync()
+            e_iters += it
+        t_e2e = time.perf_counter() - t0
+        barrier()
+        e_dofs = float(E * N ** 3 * e_iters)
+        if world > 1:
+            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+            dd = torch.tensor([e_dofs], device="cuda", dtype=torch.float64)
+            dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+            e_dofs = float(dd.item())
+        e2e = {"value": e_dofs / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": M.nL * 8,
+               "d2h_bytes_per_step": M.nL * 8, "ms_per_step": 1e3 * t_e2e / a.steps}
+        assert np.allclose(xh.numpy(), x.cpu().numpy(), rtol=0, atol=0)
+        sem.update(bh, sem.SEM_FREE)
+        sem.update(xh, sem.SEM_FREE)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cg, times = time_oracle(a, a.cpu_iters)
+        cpu = {"value": cg, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
+               "sample": f"{a.cpu_iters} FP64 CG iterations of the full E={E}, N={N} problem on one host "
+                         f"core (single-threaded C oracle, set-up excluded, {times[0]:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_of(a, world, iters_total // max(a.steps, 1)),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary(),
+                "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
+                           "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
+        print(json.dumps(line), flush=True)
+    M.free()
+    torch.cuda.synchronize()
+    sem.finalize()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * sem.h -- C-ABI of libsem, a GB300 (sm_103a) library for the spectral-element
+ * Poisson operator and its conjugate-gradient solve.
+ *
+ * The interface has the shape of the runtime calls that the paper's pragmas
+ * lower to (Section IV, Fig. "Syntax of the nomp directives", and Section V):
+ * initialise the runtime, map host arrays to and from the device, run a named
+ * kernel, synchronise, finalise.  There is no source-to-source compiler and no
+ * JIT here: every named kernel is hand-written CUDA, specialised at compile
+ * time on the polynomial order N (the role the paper gives to the "jit"
+ * clause, Section VIII-B).
+ *
+ * Conventions shared by every call
+ *   - Every function returns an int status: SEM_OK (0) or a negative SEM_E*
+ *     code.  sem_last_error() returns a message for the last failure of the
+ *     calling thread's most recent call.
+ *   - The library is single-context: one device, one stream.  Calls are not
+ *     thread-safe; serialise them.
+ *   - Device memory is obtained through the allocator installed with
+ *     sem_set_allocator (cudaMalloc/cudaFree by default).  The library never
+ *     holds host memory of the caller beyond a call, except the host base
+ *     pointers that key the device mirrors of sem_update.
+ *   - Vectors on local nodes use the layout l = i + n*(j + n*(k + n*e)),
+ *     n = N+1, i (the r direction) fastest, e = ex + nx*(ey + ny*ez).
+ *   - Device arrays passed to kernels must be 16-byte aligned.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SEM_OK          0
+#define SEM_EINIT      -1  /* not initialised, initialised twice, or finalised */
+#define SEM_EARG       -2  /* malformed argument (count, kind, value, alignment) */
+#define SEM_ENOMAP     -3  /* host array has no device mirror */
+#define SEM_ERANGE     -4  /* range outside the mirror, or size above a limit */
+#define SEM_ENOMEM     -5  /* device allocation failed or HBM budget exceeded */
+#define SEM_EKERNEL    -6  /* unknown kernel name */
+#define SEM_ETIMEDOUT  -7  /* a bounded device wait gave up (device status word) */
+#define SEM_ECUDA      -8  /* CUDA runtime error (message has the CUDA text) */
+#define SEM_EMESH      -9  /* invalid mesh: non-positive Jacobian */
+#define SEM_EHANDLE   -10  /* unknown problem handle */
+
+/* ---- sem_update operations (Section IV, Table "update operations") ------- */
+#define SEM_ALLOC 0  /* allocate the device mirror of host[start, end), no copy  */
+#define SEM_TO    1  /* copy host[start, end) to the device (allocating if needed) */
+#define SEM_FROM  2  /* copy device[start, end) back to host[start, end)          */
+#define SEM_FREE  3  /* release the device mirror                                 */
+
+/* ---- sem_run argument kinds --------------------------------------------- */
+#define SEM_ARG_INT        0  /* v.i : integer value                               */
+#define SEM_ARG_DOUBLE     1  /* v.d : double value                                */
+#define SEM_ARG_MAPPED     2  /* v.ptr : host address inside a sem_update mirror;  */
+                              /*        resolved to the device address            */
+#define SEM_ARG_DEVICE     3  /* v.ptr : device address (caller-owned memory)      */
+#define SEM_ARG_OUT_DOUBLE 4  /* v.ptr : host double*, written before sem_run      */
+                              /*        returns (sem_run then syncs its stream)   */
+#define SEM_ARG_OUT_INT    5  /* v.ptr : host int64_t*, as above                   */
+#define SEM_ARG_NONE       6  /* absent optional array                             */
+
+typedef struct sem_arg {
+    int32_t kind;
+    int32_t reserved;
+    union {
+        int64_t i;
+        double d;
+        void *ptr;
+    } v;
+} sem_arg;
+
+/* Device allocator hooks: alloc returns a device pointer (NULL on failure,
+ * 256-byte aligned or better); free releases it.  ctx is passed through. */
+typedef void *(*sem_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*sem_free_fn)(void *ptr, void *ctx);
+
+/* Initialise the runtime (Section IV: "init" takes C-style command-line
+ * arguments with runtime configuration).  Recognised arguments:
+ *   --device=K        CUDA device ordinal (default 0)
+ *   --verbose=V       0 silent (default), 1 setup messages on stderr
+ *   --hbm-budget=GB   cap on device bytes the library allocates (default: none)
+ * Unknown arguments are ignored.  A second sem_init without sem_finalize
+ * returns SEM_EINIT.  Queries the device (name, SM count, shared memory per
+ * block, the analogue of the paper's "context" table, Section V-B). */
+int sem_init(int argc, const char **argv);
+
+/* Map host arrays to and from the device (Section IV, "update" directive and
+ * its alloc/to/from/free table).  The mirror is keyed by the host base
+ * address `host` and covers elements [start, end) of size elem_size.
+ *   SEM_ALLOC  creates the mirror (SEM_EARG if one exists for `host`).
+ *   SEM_TO     copies host[start, end) into the mirror, creating it first if
+ *              `host` has none; an existing mirror must contain the range.
+ *   SEM_FROM   copies the range back; SEM_ENOMAP without a mirror, SEM_ERANGE
+ *              if the range lies outside it.
+ *   SEM_FREE   releases the mirror (SEM_ENOMAP without one).
+ * Copies are ordered on the library stream and asynchronous with respect to
+ * the host when the host memory is pinned; results of SEM_FROM are visible
+ * after sem_sync (or any sem_run that syncs).  The caller keeps ownership of
+ * the host memory; the library owns the mirror until SEM_FREE or
+ * sem_finalize.  SEM_ENOMEM if the allocation fails or exceeds the budget. */
+int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
+
+/* Run a named kernel (Section IV, "for" directive -> jit + run; the "name"
+ * clause names kernels).  Arrays are SEM_ARG_MAPPED or SEM_ARG_DEVICE; the
+ * list below gives arguments in order ([..] = optional, SEM_ARG_NONE or
+ * omitted).  Local vectors have nL = E (N+1)^3 doubles.  Kernels are launched
+ * on the library stream; a call with an OUT argument syncs before returning.
+ *
+ *   "mesh"      nx, ny, nz, N, verts[(nx+1)(ny+1)(nz+1)*3], OUT handle
+ *               Build a problem on an nx*ny*nz box of order N (1 <= N <= 9):
+ *               GLL rule, derivative matrix, trilinear geometry (6 factors
+ *               and mass weight per node, FP64), direct-stiffness map,
+ *               Dirichlet mask and multiplicity weights.  SEM_EMESH if a
+ *               Jacobian is not positive.  Vertex v = a+(nx+1)(b+(ny+1)c).
+ *   "mesh_free" handle
+ *   "info"      handle, OUT nL, OUT nG, OUT n_shared_ids, OUT n_masked
+ *   "ax"        handle, x, y            y = A_local x (per element, no sum)
+ *   "gs"        handle, u               u = QQ^T u in place; copies summed in
+ *                                       ascending local index (deterministic)
+ *   "mask"      handle, u               zero the Dirichlet-boundary copies
+ *   "axg"       handle, x, y            y = mask(QQ^T(A_local x))
+ *   "dot"       handle, u, v, OUT d     sum_l c_l u_l v_l, c = 1/multiplicity
+ *   "geom"      handle, G[nL*6], B[nL]  copy out factors (rr,rs,rt,ss,st,tt)
+ *   "nodes"     handle, X[nL*3]         nodal coordinates
+ *   "gs_map"    handle, ptr[n_shared_ids+1] int32, idx[ptr[end]] int32
+ *               copies of each shared global id (ids in the library's
+ *               internal order), copies ascending
+ *   "rhs"       handle, f, b            b = mask(QQ^T(B f))
+ *   "rhs_sin"   handle, b               f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+ *   "cg_solve"  handle, b, x, tol, maxit, OUT iters, OUT rel_res, [hist]
+ *               Unpreconditioned CG from x = 0 (Section VIII-A) until
+ *               sqrt(rho_k/rho_0) <= tol or maxit iterations (tol <= 0: exactly
+ *               maxit).  rho = <r,r>_c.  hist (maxit+1 doubles, optional)
+ *               receives sqrt(rho_k).  rel_res = sqrt(rho/rho_0) at exit.
+ *   "true_res"  handle, b, x, OUT d     ||b - A x||_c / ||b||_c (FP64)
+ *   "cg_ax"     handle                  one launch of the CG iteration's fused
+ *                                       operator kernel on the problem's own CG
+ *                                       vectors (p = r + beta p, w = A_local p,
+ *                                       <p, w>); for timing after a cg_solve
+ *   "peak_fma"  dtype (0 f64, 1 f32), iters, OUT flops_per_s
+ *               measured FMA issue rate of the FP64 or FP32 pipe (device fact
+ *               for the ALU roofline; not part of the method)
+ * Unknown names return SEM_EKERNEL; wrong argument counts or kinds SEM_EARG. */
+int sem_run(const char *kernel, int nargs, const sem_arg *args);
+
+/* Host barrier on the library stream (Section IV, "sync").  Returns
+ * SEM_ETIMEDOUT if a kernel reported a bounded wait that gave up, SEM_ECUDA
+ * on an asynchronous CUDA error. */
+int sem_sync(void);
+
+/* Release every mirror, problem, graph and the stream (Section IV,
+ * "finalize").  Later calls other than sem_init return SEM_EINIT. */
+int sem_finalize(void);
+
+/* Message for the most recent failing call (static storage, never NULL). */
+const char *sem_last_error(void);
+
+/* Install device allocator hooks (before or after sem_init; affects later
+ * allocations).  Passing NULL for both restores cudaMalloc/cudaFree. */
+int sem_set_allocator(sem_alloc_fn alloc_fn, sem_free_fn free_fn, void *ctx);
+
+/* Use `stream` (a cudaStream_t) for all later work.  NULL restores the
+ * library's own non-blocking stream.  Requires sem_init. */
+int sem_set_stream(void *stream);
+
+/* Number of kernels the library has launched since sem_init (each kernel in
+ * a replayed CUDA graph counts once per replay). */
+int64_t sem_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

@@ -1,0 +1,638 @@
+// sem_api.cu -- the C-ABI of libsem: runtime context, device allocator
+// hooks, host-array mirrors, argument marshalling and the named-kernel
+// dispatch.  The call shapes follow the runtime interface the paper's
+// pragmas lower to (init / update / run / sync / finalize, Sections IV-V).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sem.h"
+#include "sem_internal.h"
+
+namespace sem {
+namespace {
+
+struct Mirror {
+    uintptr_t host_base;   // key: host base pointer
+    size_t start, end, elem;
+    void *dev;             // device copy of host[start, end)
+};
+
+struct Context {
+    bool up = false;
+    int device = 0;
+    int verbose = 0;
+    size_t budget = 0;                 // 0: unlimited
+    size_t in_use = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t cur_stream = nullptr;
+    sem_alloc_fn alloc_fn = nullptr;
+    sem_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
+    std::map<void *, size_t> sizes;    // device pointer -> bytes
+    std::map<uintptr_t, Mirror> mirrors;
+    std::map<int64_t, Problem *> problems;
+    int64_t next_handle = 1;
+    int32_t *status_dev = nullptr;
+    int32_t *status_pinned = nullptr;
+    cudaDeviceProp prop{};
+};
+
+Context g;
+std::atomic<int64_t> g_launches{0};
+thread_local char g_err[1024] = "no error";
+
+}  // namespace
+
+int set_error(int code, const std::string &msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg.c_str());
+    return code;
+}
+
+int cuda_check(cudaError_t err, const char *what) {
+    if (err == cudaSuccess) return SEM_OK;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(err), cudaGetErrorName(err));
+    if (err == cudaErrorMemoryAllocation) return set_error(SEM_ENOMEM, buf);
+    return set_error(SEM_ECUDA, buf);
+}
+
+void *dev_alloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (g.budget && g.in_use + bytes > g.budget) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "device allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)",
+                 bytes, g.in_use, g.budget);
+        set_error(SEM_ENOMEM, buf);
+        return nullptr;
+    }
+    void *p = nullptr;
+    if (g.alloc_fn) {
+        p = g.alloc_fn(bytes, g.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (!p) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device allocation of %zu bytes failed", bytes);
+        set_error(SEM_ENOMEM, buf);
+        return nullptr;
+    }
+    if (reinterpret_cast<uintptr_t>(p) & 255u) {
+        set_error(SEM_ENOMEM, "allocator returned memory that is not 256-byte aligned");
+        if (g.free_fn) g.free_fn(p, g.alloc_ctx); else cudaFree(p);
+        return nullptr;
+    }
+    g.sizes[p] = bytes;
+    g.in_use += bytes;
+    return p;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    auto it = g.sizes.find(p);
+    if (it != g.sizes.end()) {
+        g.in_use -= it->second;
+        g.sizes.erase(it);
+    }
+    if (g.free_fn) g.free_fn(p, g.alloc_ctx); else cudaFree(p);
+}
+
+cudaStream_t stream() { return g.cur_stream; }
+int32_t *status_word() { return g.status_dev; }
+int32_t *status_host() { return g.status_pinned; }
+void count_launches(int64_t n) { g_launches += n; }
+
+int poll_status() {
+    int rc = cuda_check(cudaMemcpyAsync(g.status_pinned, g.status_dev, sizeof(int32_t),
+                                        cudaMemcpyDeviceToHost, g.cur_stream), "status read");
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(g.cur_stream), "status sync");
+    if (rc != SEM_OK) return rc;
+    if (*g.status_pinned != kStatusOk) {
+        const int32_t code = *g.status_pinned;
+        *g.status_pinned = 0;
+        cudaMemsetAsync(g.status_dev, 0, sizeof(int32_t), g.cur_stream);
+        cudaStreamSynchronize(g.cur_stream);
+        char buf[128];
+        snprintf(buf, sizeof buf, "a bounded device wait gave up (status %d)", code);
+        return set_error(SEM_ETIMEDOUT, buf);
+    }
+    return SEM_OK;
+}
+
+namespace {
+
+// ---------------------------------------------------------------- mirrors
+Mirror *find_mirror_containing(uintptr_t addr, size_t bytes) {
+    // mirrors are keyed by host base; the window is [base + start*elem, base + end*elem)
+    for (auto &kv : g.mirrors) {
+        Mirror &m = kv.second;
+        const uintptr_t lo = m.host_base + m.start * m.elem, hi = m.host_base + m.end * m.elem;
+        if (addr >= lo && addr + bytes <= hi) return &m;
+    }
+    return nullptr;
+}
+
+// ---------------------------------------------------------------- arguments
+struct ArgReader {
+    const char *kernel;
+    int nargs;
+    const sem_arg *args;
+    int err = SEM_OK;
+
+    bool need(int n) {
+        if (nargs < n) {
+            fail(SEM_EARG, "expects at least " + std::to_string(n) + " arguments");
+            return false;
+        }
+        return true;
+    }
+    int fail(int code, const std::string &msg) {
+        if (err == SEM_OK) err = set_error(code, std::string(kernel) + ": " + msg);
+        return err;
+    }
+    int64_t i(int k, const char *name) {
+        if (k >= nargs || args[k].kind != SEM_ARG_INT) {
+            fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be SEM_ARG_INT");
+            return 0;
+        }
+        return args[k].v.i;
+    }
+    double d(int k, const char *name) {
+        if (k >= nargs || (args[k].kind != SEM_ARG_DOUBLE && args[k].kind != SEM_ARG_INT)) {
+            fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be SEM_ARG_DOUBLE");
+            return 0;
+        }
+        return args[k].kind == SEM_ARG_DOUBLE ? args[k].v.d : double(args[k].v.i);
+    }
+    // device address of an array argument holding `bytes` bytes
+    void *arr(int k, size_t bytes, const char *name, bool optional = false) {
+        if (k >= nargs || args[k].kind == SEM_ARG_NONE) {
+            if (!optional)
+                fail(SEM_EARG, std::string("array argument ") + std::to_string(k) + " (" + name + ") missing");
+            return nullptr;
+        }
+        const sem_arg &a = args[k];
+        void *dev = nullptr;
+        if (a.kind == SEM_ARG_DEVICE) {
+            dev = a.v.ptr;
+        } else if (a.kind == SEM_ARG_MAPPED) {
+            const uintptr_t h = reinterpret_cast<uintptr_t>(a.v.ptr);
+            Mirror *m = find_mirror_containing(h, bytes);
+            if (!m) {
+                // distinguish "no mirror at all" from "range too small"
+                for (auto &kv : g.mirrors) {
+                    Mirror &mm = kv.second;
+                    const uintptr_t lo = mm.host_base + mm.start * mm.elem, hi = mm.host_base + mm.end * mm.elem;
+                    if (h >= lo && h < hi) {
+                        fail(SEM_ERANGE, std::string(name) + ": mirror is smaller than the array the kernel needs");
+                        return nullptr;
+                    }
+                }
+                fail(SEM_ENOMAP, std::string(name) + ": host array has no device mirror");
+                return nullptr;
+            }
+            dev = static_cast<unsigned char *>(m->dev) + (h - (m->host_base + m->start * m->elem));
+        } else {
+            fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be an array");
+            return nullptr;
+        }
+        if (!dev || (reinterpret_cast<uintptr_t>(dev) & 15u)) {
+            fail(SEM_EARG, std::string(name) + ": device array must be non-null and 16-byte aligned");
+            return nullptr;
+        }
+        return dev;
+    }
+    void *out(int k, int kind, const char *name) {
+        if (k >= nargs || args[k].kind != kind || !args[k].v.ptr) {
+            fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be an OUT pointer");
+            return nullptr;
+        }
+        return args[k].v.ptr;
+    }
+};
+
+Problem *get_problem(ArgReader &R, int k) {
+    const int64_t h = R.i(k, "handle");
+    if (R.err) return nullptr;
+    auto it = g.problems.find(h);
+    if (it == g.problems.end()) {
+        R.fail(SEM_EHANDLE, "unknown problem handle " + std::to_string(h));
+        return nullptr;
+    }
+    return it->second;
+}
+
+int sync_stream(const char *what) { return cuda_check(cudaStreamSynchronize(g.cur_stream), what); }
+
+// ---------------------------------------------------------------- named kernels
+int run_mesh(ArgReader &R) {
+    if (!R.need(6)) return R.err;
+    const int64_t nx = R.i(0, "nx"), ny = R.i(1, "ny"), nz = R.i(2, "nz"), N = R.i(3, "N");
+    if (R.err) return R.err;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+        return R.fail(SEM_EARG, "nx, ny, nz must be in [1, 2^20]");
+    const size_t nv = size_t(nx + 1) * size_t(ny + 1) * size_t(nz + 1);
+    const double *verts = static_cast<const double *>(R.arr(4, nv * 3 * sizeof(double), "verts"));
+    int64_t *out = static_cast<int64_t *>(R.out(5, SEM_ARG_OUT_INT, "handle"));
+    if (R.err) return R.err;
+    Problem *P = nullptr;
+    const int rc = problem_create(int(nx), int(ny), int(nz), int(N), verts, &P);
+    if (rc != SEM_OK) return rc;
+    const int64_t h = g.next_handle++;
+    g.problems[h] = P;
+    *out = h;
+    if (g.verbose)
+        fprintf(stderr, "[sem] mesh %lld: %dx%dx%d N=%d nL=%lld nG=%lld shared=%lld masked=%lld\n",
+                (long long)h, P->nx, P->ny, P->nz, P->N, (long long)P->nL, (long long)P->nG,
+                (long long)P->n_sh, (long long)P->n_mask);
+    return SEM_OK;
+}
+
+int run_mesh_free(ArgReader &R) {
+    if (!R.need(1)) return R.err;
+    const int64_t h = R.i(0, "handle");
+    if (R.err) return R.err;
+    auto it = g.problems.find(h);
+    if (it == g.problems.end()) return R.fail(SEM_EHANDLE, "unknown problem handle");
+    sync_stream("mesh_free");
+    problem_destroy(it->second);
+    g.problems.erase(it);
+    return SEM_OK;
+}
+
+int run_info(ArgReader &R) {
+    if (!R.need(5)) return R.err;
+    Problem *P = get_problem(R, 0);
+    int64_t *o1 = static_cast<int64_t *>(R.out(1, SEM_ARG_OUT_INT, "nL"));
+    int64_t *o2 = static_cast<int64_t *>(R.out(2, SEM_ARG_OUT_INT, "nG"));
+    int64_t *o3 = static_cast<int64_t *>(R.out(3, SEM_ARG_OUT_INT, "n_shared_ids"));
+    int64_t *o4 = static_cast<int64_t *>(R.out(4, SEM_ARG_OUT_INT, "n_masked"));
+    if (R.err) return R.err;
+    *o1 = P->nL;
+    *o2 = P->nG;
+    *o3 = P->n_sh;
+    *o4 = P->n_mask;
+    return SEM_OK;
+}
+
+int run_ax(ArgReader &R, bool assembled) {
+    if (!R.need(3)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *x = static_cast<const double *>(R.arr(1, vb, "x"));
+    double *y = static_cast<double *>(R.arr(2, vb, "y"));
+    if (R.err) return R.err;
+    if (x == y) return R.fail(SEM_EARG, "x and y must not alias");
+    int rc = launch_ax(P, x, y);
+    if (rc == SEM_OK && assembled) rc = launch_gs(P, y);
+    if (rc == SEM_OK && assembled) rc = launch_mask(P, y);
+    return rc;
+}
+
+int run_inplace(ArgReader &R, int which) {
+    if (!R.need(2)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    double *u = static_cast<double *>(R.arr(1, size_t(P->nL) * sizeof(double), "u"));
+    if (R.err) return R.err;
+    return which == 0 ? launch_gs(P, u) : launch_mask(P, u);
+}
+
+int run_dot(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *u = static_cast<const double *>(R.arr(1, vb, "u"));
+    const double *v = static_cast<const double *>(R.arr(2, vb, "v"));
+    double *out = static_cast<double *>(R.out(3, SEM_ARG_OUT_DOUBLE, "result"));
+    if (R.err) return R.err;
+    int rc = launch_dot(P, u, v);
+    if (rc != SEM_OK) return rc;
+    double val = 0.0;
+    rc = cuda_check(cudaMemcpyAsync(&P->st_host->dot_out, &P->st->dot_out, sizeof(double),
+                                    cudaMemcpyDeviceToHost, g.cur_stream), "dot: read");
+    if (rc == SEM_OK) rc = sync_stream("dot: sync");
+    if (rc == SEM_OK) val = P->st_host->dot_out;
+    *out = val;
+    return rc;
+}
+
+int run_geom(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    double *G = static_cast<double *>(R.arr(1, size_t(P->nL) * 6 * sizeof(double), "G"));
+    double *B = static_cast<double *>(R.arr(2, size_t(P->nL) * sizeof(double), "B"));
+    if (R.err) return R.err;
+    int rc = cuda_check(cudaMemcpyAsync(G, P->G, size_t(P->nL) * 6 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        g.cur_stream), "geom: copy G");
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(B, P->B, size_t(P->nL) * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        g.cur_stream), "geom: copy B");
+    return rc;
+}
+
+int run_nodes(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    double *X = static_cast<double *>(R.arr(1, size_t(P->nL) * 3 * sizeof(double), "X"));
+    if (R.err) return R.err;
+    return launch_nodes(P, nullptr, X);
+}
+
+int run_gs_map(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    int32_t *ptr = static_cast<int32_t *>(R.arr(1, size_t(P->n_sh + 1) * sizeof(int32_t), "ptr"));
+    int32_t *idx = static_cast<int32_t *>(R.arr(2, size_t(std::max<int64_t>(P->n_sh_copies, 1)) * sizeof(int32_t), "idx"));
+    if (R.err) return R.err;
+    int rc = cuda_check(cudaMemcpyAsync(ptr, P->sh_ptr, size_t(P->n_sh + 1) * sizeof(int32_t),
+                                        cudaMemcpyDeviceToDevice, g.cur_stream), "gs_map: ptr");
+    if (rc == SEM_OK && P->n_sh_copies)
+        rc = cuda_check(cudaMemcpyAsync(idx, P->sh_idx, size_t(P->n_sh_copies) * sizeof(int32_t),
+                                        cudaMemcpyDeviceToDevice, g.cur_stream), "gs_map: idx");
+    return rc;
+}
+
+int run_rhs(ArgReader &R, bool sin_source) {
+    Problem *P = nullptr;
+    if (sin_source) {
+        if (!R.need(2)) return R.err;
+        P = get_problem(R, 0);
+        if (R.err) return R.err;
+        double *b = static_cast<double *>(R.arr(1, size_t(P->nL) * sizeof(double), "b"));
+        if (R.err) return R.err;
+        return launch_rhs_sin(P, nullptr, b);
+    }
+    if (!R.need(3)) return R.err;
+    P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *f = static_cast<const double *>(R.arr(1, vb, "f"));
+    double *b = static_cast<double *>(R.arr(2, vb, "b"));
+    if (R.err) return R.err;
+    int rc = launch_scale(P, P->B, f, b);
+    if (rc == SEM_OK) rc = launch_gs(P, b);
+    if (rc == SEM_OK) rc = launch_mask(P, b);
+    return rc;
+}
+
+int run_cg_solve(ArgReader &R) {
+    if (!R.need(7)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b"));
+    double *x = static_cast<double *>(R.arr(2, vb, "x"));
+    const double tol = R.d(3, "tol");
+    const int64_t maxit = R.i(4, "maxit");
+    int64_t *oit = static_cast<int64_t *>(R.out(5, SEM_ARG_OUT_INT, "iters"));
+    double *ores = static_cast<double *>(R.out(6, SEM_ARG_OUT_DOUBLE, "rel_res"));
+    if (R.err) return R.err;
+    if (maxit < 0 || maxit > (1 << 30)) return R.fail(SEM_EARG, "maxit must be in [0, 2^30]");
+    double *hist = static_cast<double *>(R.arr(7, size_t(maxit + 1) * sizeof(double), "hist", true));
+    if (R.err) return R.err;
+    if (b == x) return R.fail(SEM_EARG, "b and x must not alias");
+    return cg_solve(P, b, x, tol, int(maxit), hist, oit, ores);
+}
+
+int run_cg_ax(ArgReader &R) {
+    if (!R.need(1)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    return launch_ax_cg(P);
+}
+
+int run_peak_fma(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    const int64_t dtype = R.i(0, "dtype"), iters = R.i(1, "iters");
+    double *out = static_cast<double *>(R.out(2, SEM_ARG_OUT_DOUBLE, "flops_per_s"));
+    if (R.err) return R.err;
+    if (dtype != 0 && dtype != 1) return R.fail(SEM_EARG, "dtype must be 0 (f64) or 1 (f32)");
+    return probe_fma_rate(int(dtype), int(iters), out);
+}
+
+int run_true_res(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b"));
+    const double *x = static_cast<const double *>(R.arr(2, vb, "x"));
+    double *out = static_cast<double *>(R.out(3, SEM_ARG_OUT_DOUBLE, "result"));
+    if (R.err) return R.err;
+    // w = A x (assembled, masked); r = b - w, both in the problem's work vectors
+    double *w = P->w, *r = P->r;
+    if (x == w || x == r || b == w || b == r) return R.fail(SEM_EARG, "arguments alias work vectors");
+    int rc = launch_ax(P, x, w);
+    if (rc == SEM_OK) rc = launch_gs(P, w);
+    if (rc == SEM_OK) rc = launch_mask(P, w);
+    if (rc == SEM_OK) rc = launch_sub(P, b, w, r);
+    double rr = 0.0, bb = 0.0;
+    for (int pass = 0; pass < 2 && rc == SEM_OK; ++pass) {
+        rc = launch_dot(P, pass == 0 ? r : b, pass == 0 ? r : b);
+        if (rc == SEM_OK)
+            rc = cuda_check(cudaMemcpyAsync(&P->st_host->dot_out, &P->st->dot_out, sizeof(double),
+                                            cudaMemcpyDeviceToHost, g.cur_stream), "true_res: read");
+        if (rc == SEM_OK) rc = sync_stream("true_res: sync");
+        if (rc == SEM_OK) (pass == 0 ? rr : bb) = P->st_host->dot_out;
+    }
+    if (rc != SEM_OK) return rc;
+    *out = bb > 0.0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    return SEM_OK;
+}
+
+}  // namespace
+}  // namespace sem
+
+using namespace sem;
+
+extern "C" {
+
+int sem_init(int argc, const char **argv) {
+    if (g.up) return set_error(SEM_EINIT, "sem_init: already initialised");
+    int device = 0, verbose = 0;
+    double budget_gb = 0.0;
+    for (int a = 0; a < argc; ++a) {
+        if (!argv || !argv[a]) continue;
+        const char *s = argv[a];
+        if (!strncmp(s, "--device=", 9)) device = atoi(s + 9);
+        else if (!strncmp(s, "--verbose=", 10)) verbose = atoi(s + 10);
+        else if (!strncmp(s, "--hbm-budget=", 13)) budget_gb = atof(s + 13);
+    }
+    int rc = cuda_check(cudaSetDevice(device), "sem_init: cudaSetDevice");
+    if (rc != SEM_OK) return rc;
+    rc = cuda_check(cudaGetDeviceProperties(&g.prop, device), "sem_init: device query");
+    if (rc != SEM_OK) return rc;
+    rc = cuda_check(cudaStreamCreateWithFlags(&g.own_stream, cudaStreamNonBlocking), "sem_init: stream");
+    if (rc != SEM_OK) return rc;
+    g.cur_stream = g.own_stream;
+    g.device = device;
+    g.verbose = verbose;
+    g.budget = budget_gb > 0 ? size_t(budget_gb * 1e9) : 0;
+    g.in_use = 0;
+    g.up = true;
+    g.status_dev = static_cast<int32_t *>(dev_alloc(sizeof(int32_t) * 4));
+    if (!g.status_dev) {
+        g.up = false;
+        return SEM_ENOMEM;
+    }
+    rc = cuda_check(cudaMallocHost(&g.status_pinned, sizeof(int32_t) * 4), "sem_init: pinned status");
+    if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(g.status_dev, 0, sizeof(int32_t) * 4, g.cur_stream), "sem_init");
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(g.cur_stream), "sem_init: sync");
+    if (rc != SEM_OK) {
+        g.up = false;
+        return rc;
+    }
+    g_launches = 0;
+    if (verbose)
+        fprintf(stderr, "[sem] device %d: %s, %d SMs, cc %d.%d, %zu KB smem/block (opt-in)\n", device,
+                g.prop.name, g.prop.multiProcessorCount, g.prop.major, g.prop.minor,
+                size_t(g.prop.sharedMemPerBlockOptin) / 1024);
+    return SEM_OK;
+}
+
+int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op) {
+    if (!g.up) return set_error(SEM_EINIT, "sem_update: not initialised");
+    if (!host || elem_size == 0 || end < start) return set_error(SEM_EARG, "sem_update: bad host pointer or range");
+    const uintptr_t key = reinterpret_cast<uintptr_t>(host);
+    auto it = g.mirrors.find(key);
+    switch (op) {
+        case SEM_ALLOC:
+        case SEM_TO: {
+            if (it == g.mirrors.end()) {
+                if (end == start) return set_error(SEM_EARG, "sem_update: empty range");
+                Mirror m{key, start, end, elem_size, nullptr};
+                m.dev = dev_alloc((end - start) * elem_size);
+                if (!m.dev) return SEM_ENOMEM;
+                it = g.mirrors.emplace(key, m).first;
+            } else if (op == SEM_ALLOC) {
+                return set_error(SEM_EARG, "sem_update(alloc): host array already has a mirror");
+            }
+            if (op == SEM_TO) {
+                Mirror &m = it->second;
+                if (elem_size != m.elem || start < m.start || end > m.end)
+                    return set_error(SEM_ERANGE, "sem_update(to): range outside the mirror");
+                if (end > start)
+                    return cuda_check(cudaMemcpyAsync(static_cast<unsigned char *>(m.dev) + (start - m.start) * m.elem,
+                                                      static_cast<unsigned char *>(host) + start * m.elem,
+                                                      (end - start) * m.elem, cudaMemcpyHostToDevice, g.cur_stream),
+                                      "sem_update(to)");
+            }
+            return SEM_OK;
+        }
+        case SEM_FROM: {
+            if (it == g.mirrors.end()) return set_error(SEM_ENOMAP, "sem_update(from): host array has no mirror");
+            Mirror &m = it->second;
+            if (elem_size != m.elem || start < m.start || end > m.end)
+                return set_error(SEM_ERANGE, "sem_update(from): range outside the mirror");
+            if (end > start)
+                return cuda_check(cudaMemcpyAsync(static_cast<unsigned char *>(host) + start * m.elem,
+                                                  static_cast<unsigned char *>(m.dev) + (start - m.start) * m.elem,
+                                                  (end - start) * m.elem, cudaMemcpyDeviceToHost, g.cur_stream),
+                                  "sem_update(from)");
+            return SEM_OK;
+        }
+        case SEM_FREE: {
+            if (it == g.mirrors.end()) return set_error(SEM_ENOMAP, "sem_update(free): host array has no mirror");
+            cudaStreamSynchronize(g.cur_stream);
+            dev_free(it->second.dev);
+            g.mirrors.erase(it);
+            return SEM_OK;
+        }
+        default:
+            return set_error(SEM_EARG, "sem_update: unknown operation");
+    }
+}
+
+int sem_run(const char *kernel, int nargs, const sem_arg *args) {
+    if (!g.up) return set_error(SEM_EINIT, "sem_run: not initialised");
+    if (!kernel) return set_error(SEM_EARG, "sem_run: kernel name is NULL");
+    if (nargs < 0 || (nargs > 0 && !args)) return set_error(SEM_EARG, "sem_run: bad argument list");
+    ArgReader R{kernel, nargs, args};
+    const std::string k(kernel);
+    int rc;
+    if (k == "mesh") rc = run_mesh(R);
+    else if (k == "mesh_free") rc = run_mesh_free(R);
+    else if (k == "info") rc = run_info(R);
+    else if (k == "ax") rc = run_ax(R, false);
+    else if (k == "axg") rc = run_ax(R, true);
+    else if (k == "gs") rc = run_inplace(R, 0);
+    else if (k == "mask") rc = run_inplace(R, 1);
+    else if (k == "dot") rc = run_dot(R);
+    else if (k == "geom") rc = run_geom(R);
+    else if (k == "nodes") rc = run_nodes(R);
+    else if (k == "gs_map") rc = run_gs_map(R);
+    else if (k == "rhs") rc = run_rhs(R, false);
+    else if (k == "rhs_sin") rc = run_rhs(R, true);
+    else if (k == "cg_solve") rc = run_cg_solve(R);
+    else if (k == "true_res") rc = run_true_res(R);
+    else if (k == "cg_ax") rc = run_cg_ax(R);
+    else if (k == "peak_fma") rc = run_peak_fma(R);
+    else return set_error(SEM_EKERNEL, "sem_run: unknown kernel '" + k + "'");
+    return rc;
+}
+
+int sem_sync(void) {
+    if (!g.up) return set_error(SEM_EINIT, "sem_sync: not initialised");
+    int rc = cuda_check(cudaStreamSynchronize(g.cur_stream), "sem_sync");
+    if (rc != SEM_OK) return rc;
+    return poll_status();
+}
+
+int sem_finalize(void) {
+    if (!g.up) return set_error(SEM_EINIT, "sem_finalize: not initialised");
+    cudaStreamSynchronize(g.cur_stream);
+    for (auto &kv : g.problems) problem_destroy(kv.second);
+    g.problems.clear();
+    for (auto &kv : g.mirrors) dev_free(kv.second.dev);
+    g.mirrors.clear();
+    dev_free(g.status_dev);
+    g.status_dev = nullptr;
+    if (g.status_pinned) cudaFreeHost(g.status_pinned);
+    g.status_pinned = nullptr;
+    if (g.own_stream) cudaStreamDestroy(g.own_stream);
+    g.own_stream = nullptr;
+    g.cur_stream = nullptr;
+    g.sizes.clear();
+    g.in_use = 0;
+    g.up = false;
+    return SEM_OK;
+}
+
+const char *sem_last_error(void) { return g_err; }
+
+int sem_set_allocator(sem_alloc_fn alloc_fn, sem_free_fn free_fn, void *ctx) {
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return set_error(SEM_EARG, "sem_set_allocator: give both hooks or neither");
+    if (!g.sizes.empty()) return set_error(SEM_EARG, "sem_set_allocator: device memory is still allocated");
+    g.alloc_fn = alloc_fn;
+    g.free_fn = free_fn;
+    g.alloc_ctx = ctx;
+    return SEM_OK;
+}
+
+int sem_set_stream(void *s) {
+    if (!g.up) return set_error(SEM_EINIT, "sem_set_stream: not initialised");
+    cudaStreamSynchronize(g.cur_stream);
+    g.cur_stream = s ? static_cast<cudaStream_t>(s) : g.own_stream;
+    return SEM_OK;
+}
+
+int64_t sem_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

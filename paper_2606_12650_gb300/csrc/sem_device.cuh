@@ -1,0 +1,175 @@
+// sem_device.cuh -- device helpers: TMA bulk copies with mbarriers (bounded
+// waits), deterministic block reductions, last-block tickets.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sem_internal.h"
+
+namespace sem {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    // make the initialised barrier visible to the async (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `phase` of the barrier for at most ~limit_ns.  On time-out
+// the status word records it and false is returned.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int32_t *status,
+                                                  uint64_t limit_ns = 1000000000ull) {
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if (global_ns() - t0 > limit_ns) {
+            if (status) atomicExch(status, (int32_t)kStatusMbarTimeout);
+            return false;
+        }
+    }
+}
+
+// 1D bulk copy global -> shared (TMA engine), completion counted in bytes on
+// the mbarrier.  dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Plan of a slab copy: the 16-byte-aligned middle goes through the TMA
+// engine; the ragged head/tail (< 16 bytes each) through plain loads.
+struct SlabPlan {
+    uint32_t head_bytes;   // bytes before the first 16-byte boundary
+    uint32_t mid_bytes;    // multiple of 16
+    uint32_t total_bytes;
+};
+
+__device__ __forceinline__ SlabPlan slab_plan(const void *src, uint32_t bytes) {
+    const uintptr_t s = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t t = s + bytes;
+    uintptr_t s16 = (s + 15) & ~uintptr_t(15);
+    uintptr_t t16 = t & ~uintptr_t(15);
+    SlabPlan p;
+    if (t16 <= s16) {  // no aligned middle: everything by plain loads
+        p.head_bytes = bytes;
+        p.mid_bytes = 0;
+    } else {
+        p.head_bytes = static_cast<uint32_t>(s16 - s);
+        p.mid_bytes = static_cast<uint32_t>(t16 - s16);
+    }
+    p.total_bytes = bytes;
+    return p;
+}
+
+// Returns the shared-memory address at which element 0 of a slab whose global
+// source is `src` must be placed inside a 16-byte-aligned buffer `buf` so that
+// the aligned middle lands on a 16-byte boundary.
+template <typename T>
+__device__ __forceinline__ T *slab_dst(void *buf, const T *src) {
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(src) & 15u;
+    return reinterpret_cast<T *>(static_cast<unsigned char *>(buf) + mis);
+}
+
+// Issue the TMA part of a slab copy (one thread).
+template <typename T>
+__device__ __forceinline__ void slab_issue(T *dst, const T *src, const SlabPlan &p,
+                                           uint64_t *bar) {
+    if (p.mid_bytes) {
+        const unsigned char *s = reinterpret_cast<const unsigned char *>(src) + p.head_bytes;
+        unsigned char *d = reinterpret_cast<unsigned char *>(dst) + p.head_bytes;
+        bulk_g2s(d, s, p.mid_bytes, bar);
+    }
+}
+
+// Plain-load part of a slab copy (ragged head and tail), element-wise,
+// spread over threads [t0, t0 + nthreads).
+template <typename T>
+__device__ __forceinline__ void slab_edges(T *dst, const T *src, const SlabPlan &p, int t,
+                                           int nthreads) {
+    const uint32_t n_head = p.head_bytes / sizeof(T);
+    const uint32_t n_tot = p.total_bytes / sizeof(T);
+    const uint32_t tail0 = (p.head_bytes + p.mid_bytes) / sizeof(T);
+    for (uint32_t q = t; q < n_head; q += nthreads) dst[q] = src[q];
+    for (uint32_t q = tail0 + t; q < n_tot; q += nthreads) dst[q] = src[q];
+}
+
+// Deterministic block sum (fixed shuffle tree, then fixed cross-warp tree).
+// blockDim.x must be a multiple of 32.  The result is valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *sbuf /* >= 32 */) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? sbuf[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// Publish this block's partial and find out whether it is the last block to
+// do so.  Thread 0 writes partials[blockIdx.x]; all threads get the answer.
+__device__ __forceinline__ bool publish_partial(double v0, double *partials, uint32_t *ticket) {
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = v0;
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// In the last block: sum partials[0..n) in a fixed order (strided per thread,
+// then block_sum).  Resets the ticket for the next launch.  Result in thread 0.
+__device__ __forceinline__ double finish_partials(const double *partials, int n, uint32_t *ticket,
+                                                  double *sbuf) {
+    __threadfence();
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) acc += __ldcg(partials + q);
+    acc = block_sum(acc, sbuf);
+    if (threadIdx.x == 0) *ticket = 0u;
+    return acc;
+}
+
+}  // namespace sem

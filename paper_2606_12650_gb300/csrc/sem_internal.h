@@ -1,0 +1,119 @@
+// sem_internal.h -- types and launchers shared by the libsem translation units.
+//
+// Not part of the public ABI (include/sem.h is).  Everything here is plain
+// C++/CUDA for sm_103a; no torch types.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "sem.h"
+
+namespace sem {
+
+constexpr int kMaxQ = 10;          // N <= 9  ->  N+1 <= 10 points per direction
+constexpr int kMaxPartials = 1 << 17;
+
+// Small per-problem constants passed to kernels by value (constant bank).
+struct OpConsts {
+    double D[kMaxQ * kMaxQ];       // D[i*nq + l] = l_l'(xi_i)
+    double xi[kMaxQ];
+    double w[kMaxQ];
+};
+
+// Device-resident CG state: scalars of the recurrences, the iteration
+// counter, the stop flag and the tickets of the last-block reductions.
+struct CgState {
+    double rho;        // <r_k, r_k>
+    double rho0;       // <r_0, r_0>
+    double alpha;
+    double beta;
+    double pap;        // <p, A p>
+    double tol;        // stop when sqrt(rho/rho0) <= tol (tol <= 0: never)
+    double dot_out;    // result slot of the "dot" kernel
+    double spare;
+    double *hist;      // optional: hist[k] = sqrt(rho_k)
+    int32_t iter;
+    int32_t maxit;
+    int32_t done;
+    int32_t pad0;
+    uint32_t ticket_ax;
+    uint32_t ticket_up;
+    uint32_t ticket_dot;
+    uint32_t pad1;
+};
+
+// Status word written by kernels whose bounded waits give up.
+enum DeviceStatus : int32_t {
+    kStatusOk = 0,
+    kStatusMbarTimeout = 1,
+};
+
+struct Problem {
+    int nx = 0, ny = 0, nz = 0, N = 0, nq = 0;
+    int64_t E = 0, np = 0, nL = 0, nG = 0;
+    OpConsts oc{};
+    double *verts = nullptr;       // [(nx+1)(ny+1)(nz+1)][3] device copy of the vertices
+
+    // geometry (FP64): G interleaved per node [nL][6] = (rr, rs, rt, ss, st, tt)
+    double *G = nullptr;
+    double *B = nullptr;           // [nL] mass weights W |J|
+    double *c = nullptr;           // [nL] 1 / multiplicity
+
+    // direct-stiffness sum: global ids with >= 2 copies, copies ascending
+    int32_t *sh_ptr = nullptr, *sh_idx = nullptr;
+    int64_t n_sh = 0, n_sh_copies = 0;
+    // Dirichlet mask: local indices on the cube boundary
+    int32_t *msk_idx = nullptr;
+    int64_t n_mask = 0;
+    // unmasked global ids (any multiplicity), copies ascending: fused update
+    int32_t *un_ptr = nullptr, *un_idx = nullptr;
+    int64_t n_un = 0, n_un_copies = 0;
+
+    // CG work vectors and state
+    double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr;
+    double *partials = nullptr;
+    CgState *st = nullptr;
+    CgState *st_host = nullptr;    // pinned mirror for polling
+    cudaGraphExec_t graph = nullptr;
+    int graph_iters = 0;
+    cudaStream_t graph_stream = nullptr;
+};
+
+// ---- runtime services (sem_api.cu) ---------------------------------------
+void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
+void dev_free(void *p);
+cudaStream_t stream();
+int32_t *status_word();            // device status word (kernels write it)
+int32_t *status_host();            // pinned host copy (filled by poll_status / cg_solve)
+int poll_status();                 // sync, read and clear the status word -> SEM_OK/SEM_ETIMEDOUT
+void count_launches(int64_t n);
+int set_error(int code, const std::string &msg);
+int cuda_check(cudaError_t err, const char *what);
+
+// ---- setup (sem_setup.cu) --------------------------------------------------
+int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out);
+void problem_destroy(Problem *P);
+int launch_nodes(const Problem *P, const double *verts_dev, double *X);
+int launch_rhs_sin(const Problem *P, const double *verts_dev_or_null, double *b);
+int launch_scale(const Problem *P, const double *a, const double *f, double *out);
+
+// ---- operators (sem_ax.cu, sem_cg.cu) --------------------------------------
+int prepare_ax(const Problem *P);             // kernel attributes (before any capture)
+int launch_ax(const Problem *P, const double *x, double *y);
+int launch_ax_cg(const Problem *P);          // p = r + beta p; w = A_local p; <p,w>
+int launch_gs(const Problem *P, double *u);
+int launch_mask(const Problem *P, double *u);
+int launch_dot(const Problem *P, const double *u, const double *v);  // -> st->dot_out
+int launch_sub(const Problem *P, const double *a, const double *b, double *out);  // out = a - b
+int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, double *hist);
+int launch_cg_update(const Problem *P);
+int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, double *hist,
+             int64_t *iters, double *rel_res);
+
+// ---- device facts (sem_probe.cu) --------------------------------------------
+int probe_fma_rate(int dtype, int iters, double *flops_per_s);   // dtype 0: f64, 1: f32
+
+}  // namespace sem

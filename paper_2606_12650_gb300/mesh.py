@@ -1,0 +1,81 @@
+"""``Mesh``: one box-mesh Poisson problem held by libsem, addressed by handle.
+
+Each method is one ``sem.run`` call (argument marshalling only).  Vectors are
+CUDA tensors of float64 on local nodes (``nL = E (N+1)^3`` entries, layout
+``l = i + n(j + n(k + n e))``), or host arrays mirrored with ``sem.update``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sem
+
+
+class Mesh:
+    def __init__(self, nx: int, ny: int, nz: int, N: int, verts):
+        self.nx, self.ny, self.nz, self.N = int(nx), int(ny), int(nz), int(N)
+        h = sem.OutInt()
+        if isinstance(verts, np.ndarray):
+            v = np.ascontiguousarray(verts, dtype=np.float64)
+            sem.update(v, sem.SEM_TO)
+            try:
+                sem.run("mesh", self.nx, self.ny, self.nz, self.N, v, h)
+            finally:
+                sem.update(v, sem.SEM_FREE)
+        else:
+            sem.run("mesh", self.nx, self.ny, self.nz, self.N, verts, h)
+        self.handle = h.value
+        i = [sem.OutInt() for _ in range(4)]
+        sem.run("info", self.handle, *i)
+        self.nL, self.nG, self.n_shared, self.n_masked = (o.value for o in i)
+        self.E = self.nx * self.ny * self.nz
+
+    # operators -------------------------------------------------------------
+    def ax(self, x, y):
+        sem.run("ax", self.handle, x, y)
+
+    def axg(self, x, y):
+        sem.run("axg", self.handle, x, y)
+
+    def gs(self, u):
+        sem.run("gs", self.handle, u)
+
+    def mask(self, u):
+        sem.run("mask", self.handle, u)
+
+    def dot(self, u, v) -> float:
+        o = sem.OutDouble()
+        sem.run("dot", self.handle, u, v, o)
+        return o.value
+
+    # set-up products -------------------------------------------------------
+    def geom(self, G, B):
+        sem.run("geom", self.handle, G, B)
+
+    def nodes(self, X):
+        sem.run("nodes", self.handle, X)
+
+    def gs_map(self, ptr, idx):
+        sem.run("gs_map", self.handle, ptr, idx)
+
+    def rhs(self, f, b):
+        sem.run("rhs", self.handle, f, b)
+
+    def rhs_sin(self, b):
+        sem.run("rhs_sin", self.handle, b)
+
+    # solver ----------------------------------------------------------------
+    def cg_solve(self, b, x, tol: float, maxit: int, hist=None):
+        it, res = sem.OutInt(), sem.OutDouble()
+        sem.run("cg_solve", self.handle, b, x, float(tol), int(maxit), it, res, hist)
+        return it.value, res.value
+
+    def true_res(self, b, x) -> float:
+        o = sem.OutDouble()
+        sem.run("true_res", self.handle, b, x, o)
+        return o.value
+
+    def free(self):
+        if self.handle:
+            sem.run("mesh_free", self.handle)
+            self.handle = 0

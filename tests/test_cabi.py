@@ -1,0 +1,78 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every function include/sem.h declares, and refuses work before sem_init."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(sem_[a-z_0-9]+)\s*\(", text, re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_12650_gb300 import build, sem
+    build.build()
+    return sem.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared("sem.h")
+    for must in ("sem_init", "sem_update", "sem_run", "sem_sync", "sem_finalize"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared("sem.h"):
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_exports():
+    from paper_2606_12650_gb300 import sem
+    assert set(sem.EXPORTS) <= set(_declared("sem.h"))
+
+
+def test_calls_before_init_return_einit(lib):
+    from paper_2606_12650_gb300 import sem
+    buf = (ctypes.c_double * 4)()
+    assert lib.sem_update(ctypes.cast(buf, ctypes.c_void_p), 0, 4, 8, sem.SEM_TO) == sem.SEM_EINIT
+    assert "not initialised" in sem.last_error()
+    assert lib.sem_run(b"ax", 0, None) == sem.SEM_EINIT
+    assert lib.sem_sync() == sem.SEM_EINIT
+    assert lib.sem_finalize() == sem.SEM_EINIT
+    assert lib.sem_set_stream(None) == sem.SEM_EINIT
+
+
+def test_allocator_hooks_must_come_in_pairs(lib):
+    from paper_2606_12650_gb300 import sem
+    fn = sem.ALLOC_FN(lambda n, c: 0)
+    assert lib.sem_set_allocator(ctypes.cast(fn, ctypes.c_void_p), None, None) == sem.SEM_EARG
+    assert lib.sem_set_allocator(None, None, None) == sem.SEM_OK
+
+
+def test_marshalling_kinds():
+    import numpy as np
+    from paper_2606_12650_gb300 import sem
+    assert sem._marshal(3).kind == sem.ARG_INT
+    assert sem._marshal(2.5).kind == sem.ARG_DOUBLE
+    assert sem._marshal(None).kind == sem.ARG_NONE
+    assert sem._marshal(np.zeros(4)).kind == sem.ARG_MAPPED
+    assert sem._marshal(sem.OutInt()).kind == sem.ARG_OUT_INT
+    assert sem._marshal(sem.OutDouble()).kind == sem.ARG_OUT_DOUBLE
+    assert sem._marshal(sem.DevicePtr(256)).kind == sem.ARG_DEVICE
+    with pytest.raises(TypeError):
+        sem._marshal(True)
+    with pytest.raises(ValueError):
+        sem._marshal(np.zeros((4, 4))[:, 1])
+
+
+def test_product_path_fails_loudly_without_library(tmp_path):
+    from paper_2606_12650_gb300 import sem
+    with pytest.raises(RuntimeError, match="libsem.so not found"):
+        sem._open(str(tmp_path / "missing.so"))
