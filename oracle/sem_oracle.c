@@ -174,7 +174,10 @@ void orc_nodes(int nx, int ny, int nz, int N, const double *verts,
 /* ------------------------------------------------------------------------ */
 /* Geometric factors.  J_ab = dx_a/dr_b is obtained by applying D along     */
 /* r, s, t to the nodal coordinates (exact for a trilinear map, whose degree */
-/* per direction is 1 <= N).  Then, with W = w_i w_j w_k:                    */
+/* per direction is 1 <= N).  The coordinates are taken relative to the      */
+/* element's first node: D annihilates constants, so this is the same        */
+/* derivative, without the cancellation of O(1) coordinates against O(h)    */
+/* derivatives that costs digits at high N.  Then, with W = w_i w_j w_k:     */
 /*   B = W |J|,   G = W |J| J^-1 J^-T  stored as (rr, rs, rt, ss, st, tt).   */
 /* Returns 0, or the 1-based local index of the first node with |J| <= 0    */
 /* as a negative number (an invalid mesh).                                   */
@@ -191,13 +194,14 @@ long orc_geometry(long E, int N, const double *X, const double *D,
         double J[3][3];   /* J[a][b] = dx_a / dr_b */
         for (int a = 0; a < 3; ++a) {
             double dr = 0.0, ds = 0.0, dt = 0.0;
+            double x0 = X[3 * ((long)n * n * n * e) + a];
             for (int m = 0; m < n; ++m) {
                 long lr = m + n * (j + n * (k + (long)n * e));
                 long ls = i + n * (m + n * (k + (long)n * e));
                 long lt = i + n * (j + n * (m + (long)n * e));
-                dr += D[i * n + m] * X[3 * lr + a];
-                ds += D[j * n + m] * X[3 * ls + a];
-                dt += D[k * n + m] * X[3 * lt + a];
+                dr += D[i * n + m] * (X[3 * lr + a] - x0);
+                ds += D[j * n + m] * (X[3 * ls + a] - x0);
+                dt += D[k * n + m] * (X[3 * lt + a] - x0);
             }
             J[a][0] = dr; J[a][1] = ds; J[a][2] = dt;
         }
