@@ -141,7 +141,8 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   "cg_ax"     handle                  one launch of the CG iteration's fused
  *                                       operator kernel on the problem's own CG
  *                                       vectors (p = r + beta p, w = A_local p,
- *                                       <p, w>); for timing after a cg_solve
+ *                                       <p, w>), with the stop flag cleared; for
+ *                                       timing after a cg_solve (changes p)
  *   "peak_fma"  dtype (0 f64, 1 f32), iters, OUT flops_per_s
  *               measured FMA issue rate of the FP64 or FP32 pipe (device fact
  *               for the ALU roofline; not part of the method)

@@ -414,7 +414,9 @@ int run_cg_ax(ArgReader &R) {
     if (!R.need(1)) return R.err;
     Problem *P = get_problem(R, 0);
     if (R.err) return R.err;
-    return launch_ax_cg(P);
+    // clear the stop flag a finished solve leaves behind, so the kernel does its work
+    const int rc = cuda_check(cudaMemsetAsync(&P->st->done, 0, sizeof(int32_t), g.cur_stream), "cg_ax: flag");
+    return rc != SEM_OK ? rc : launch_ax_cg(P);
 }
 
 int run_peak_fma(ArgReader &R) {
