@@ -173,6 +173,31 @@ int sem_set_stream(void *stream);
  * a replayed CUDA graph counts once per replay). */
 int64_t sem_launch_count(void);
 
+/* Weighted dot product that allocates nothing on the device.  The paper has
+ * no counterpart; this is a service for callers that cannot allocate device
+ * memory: code running while a CUDA graph is captured in a mode that forbids
+ * allocation, real-time loops that must not enter an allocator after
+ * start-up, and programs whose device memory belongs to another framework's
+ * allocator with no hook libsem could use.  The regular "dot" kernel needs a
+ * partials buffer that libsem allocates; this variant keeps its scratch (the
+ * per-block partial sums and a ticket counter) in a static device array of
+ * 64 KB that every GPU loading libsem holds until the process exits.
+ *   c, u, v  device arrays of n doubles (c may be NULL: all weights 1)
+ *   n        number of entries, 0 <= n <= 16,777,216 (SEM_ERANGE above:
+ *            the static array holds one partial per 2048 entries)
+ *   out      device double receiving sum_l c_l u_l v_l
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream)
+ * Arrays must be 8-byte aligned (SEM_EARG otherwise).  Needs no sem_init and
+ * does not synchronise: *out is valid once `stream` has reached the end of
+ * the call's work.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current), which may
+ * load the library's device code; make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * the ticket counter is cleared at the start of each call.  Calls whose work
+ * overlaps on the GPU (e.g. on two unordered streams) race on the array. */
+int sem_dot_noalloc(const double *c, const double *u, const double *v, int64_t n, double *out,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

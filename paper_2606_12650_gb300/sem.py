@@ -43,7 +43,7 @@ SEM_ALLOC, SEM_TO, SEM_FROM, SEM_FREE = 0, 1, 2, 3
 ARG_INT, ARG_DOUBLE, ARG_MAPPED, ARG_DEVICE, ARG_OUT_DOUBLE, ARG_OUT_INT, ARG_NONE = range(7)
 
 EXPORTS = ("sem_init", "sem_update", "sem_run", "sem_sync", "sem_finalize", "sem_last_error",
-           "sem_set_allocator", "sem_set_stream", "sem_launch_count")
+           "sem_set_allocator", "sem_set_stream", "sem_launch_count", "sem_dot_noalloc")
 
 
 class SemError(RuntimeError):
@@ -97,6 +97,9 @@ def load(path: str | None = None):
         lib.sem_set_stream.argtypes = [ctypes.c_void_p]
         lib.sem_launch_count.argtypes = []
         lib.sem_launch_count.restype = ctypes.c_int64
+        lib.sem_dot_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+        lib.sem_dot_noalloc.restype = ctypes.c_int
         for name in ("sem_init", "sem_update", "sem_run", "sem_sync", "sem_finalize",
                      "sem_set_allocator", "sem_set_stream"):
             getattr(lib, name).restype = ctypes.c_int
@@ -262,6 +265,16 @@ def set_stream(stream_handle: int | None) -> None:
 
 def launch_count() -> int:
     return int(load().sem_launch_count())
+
+
+def dot_noalloc(c, u, v, n: int, out, stream_handle: int | None = None) -> None:
+    """sem_dot_noalloc: out[0] = sum c*u*v over n entries, with no device
+    allocation (c may be None).  Arguments are CUDA tensors; the call does not
+    synchronise ``stream_handle`` (a cudaStream_t, None = default stream)."""
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(load().sem_dot_noalloc(ptr(c), ptr(u), ptr(v), int(n), ptr(out),
+                                  None if stream_handle is None else ctypes.c_void_p(stream_handle)),
+           "sem_dot_noalloc")
 
 
 def stream():
