@@ -11,11 +11,11 @@
 // CG (Nekbone without preconditioner, Section VIII-A).  One iteration is two
 // kernels:
 //   1. ax_f64_kernel<CG>: p = r + beta p; w = A_local p; <p, A p>; alpha
-//   2. cg_update_kernel: for every unmasked global id, the copies of w are
-//      summed in ascending local index (the direct-stiffness sum), then
-//      x += alpha p and r -= alpha (QQ^T w) are written to every copy, and
-//      <r, r> is accumulated once per global id; the last block forms
-//      rho, beta, the iteration count and the stop flag.
+//   2. cg_update_box_kernel: every local node sums the copies of w of its
+//      global node in ascending local index (the direct-stiffness sum), then
+//      applies x += alpha p and r -= alpha (QQ^T w) to itself; <r, r> is
+//      accumulated once per global node; the last block forms rho, beta, the
+//      iteration count and the stop flag.
 // The dot products of the paper are tree reductions (Section VIII-B, the
 // unrolled reduction of Table "HIP-variable vs HIP-fixed"); here each block
 // reduces in a fixed order and the last block to finish sums the per-block
@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "sem_box.cuh"
 #include "sem_device.cuh"
 #include "sem_internal.h"
 
@@ -156,28 +157,32 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
     return cuda_check(cudaGetLastError(), "cg_init_kernel");
 }
 
-__global__ void cg_update_kernel(double *__restrict__ x, double *__restrict__ r,
-                                 const double *__restrict__ p, const double *__restrict__ w,
-                                 const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                 int64_t nun, double *partials, CgState *st) {
+// Fused direct-stiffness sum + CG update, one thread per local node in the
+// natural (coalesced) order.  Every copy of a global node adds all copies of
+// w in ascending local index (same bits at each copy), then updates its own
+// x and r; x, p and r are continuous, so every copy computes the same values.
+// <r, r> counts each global node once, at its first copy.  Masked nodes are
+// left at zero.
+template <int NQ>
+__global__ void __launch_bounds__(256) cg_update_box_kernel(double *__restrict__ x, double *__restrict__ r,
+                                                            const double *__restrict__ p,
+                                                            const double *__restrict__ w, int64_t nL, int nx,
+                                                            int ny, int nz, double *partials, CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     const double alpha = st->alpha;
     double acc = 0.0;
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t < nun) {
-        const int32_t b0 = ptr[t], b1 = ptr[t + 1];
-        const int32_t l0 = idx[b0];
-        double ws = w[l0];
-        for (int32_t q = b0 + 1; q < b1; ++q) ws += w[idx[q]];
-        const double xn = fma(alpha, p[l0], x[l0]);
-        const double rn = fma(-alpha, ws, r[l0]);
-        for (int32_t q = b0; q < b1; ++q) {
-            const int32_t l = idx[q];
-            x[l] = xn;
-            r[l] = rn;
-        }
-        acc = rn * rn;
+    for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < nL;
+         l += int64_t(gridDim.x) * blockDim.x) {
+        const BoxCopies cp = box_copies<NQ>(l, nx, ny, nz);
+        if (cp.n == 0) continue;
+        double ws = __ldg(w + cp.l[0]);
+        for (int c = 1; c < cp.n; ++c) ws += __ldg(w + cp.l[c]);
+        const double xn = fma(alpha, p[l], x[l]);
+        const double rn = fma(-alpha, ws, r[l]);
+        x[l] = xn;
+        r[l] = rn;
+        if (cp.owner) acc = fma(rn, rn, acc);
     }
     const double bs = block_sum(acc, red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
@@ -195,13 +200,29 @@ __global__ void cg_update_kernel(double *__restrict__ x, double *__restrict__ r,
     }
 }
 
-int launch_cg_update(const Problem *P) {
-    const unsigned blocks = grid_for(P->n_un, kThreads);
-    if (blocks > unsigned(kMaxPartials)) return set_error(SEM_ERANGE, "cg: too many global ids");
-    cg_update_kernel<<<blocks, kThreads, 0, stream()>>>(P->x, P->r, P->p, P->w, P->un_ptr, P->un_idx,
-                                                        P->n_un, P->partials, P->st);
+template <int NQ>
+static int launch_update_nq(const Problem *P) {
+    int64_t blocks = (P->nL + kThreads - 1) / kThreads;
+    if (blocks > 152 * 64) blocks = 152 * 64;   // grid-stride beyond 9728 blocks
+    cg_update_box_kernel<NQ><<<unsigned(blocks), kThreads, 0, stream()>>>(P->x, P->r, P->p, P->w, P->nL, P->nx,
+                                                                          P->ny, P->nz, P->partials, P->st);
     count_launches(1);
-    return cuda_check(cudaGetLastError(), "cg_update_kernel");
+    return cuda_check(cudaGetLastError(), "cg_update_box_kernel");
+}
+
+int launch_cg_update(const Problem *P) {
+    switch (P->nq) {
+        case 2: return launch_update_nq<2>(P);
+        case 3: return launch_update_nq<3>(P);
+        case 4: return launch_update_nq<4>(P);
+        case 5: return launch_update_nq<5>(P);
+        case 6: return launch_update_nq<6>(P);
+        case 7: return launch_update_nq<7>(P);
+        case 8: return launch_update_nq<8>(P);
+        case 9: return launch_update_nq<9>(P);
+        case 10: return launch_update_nq<10>(P);
+        default: return set_error(SEM_EARG, "cg: unsupported order");
+    }
 }
 
 // Iterations per captured graph: the host polls the stop flag once per replay.

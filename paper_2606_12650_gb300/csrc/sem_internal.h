@@ -68,9 +68,6 @@ struct Problem {
     // Dirichlet mask: local indices on the cube boundary
     int32_t *msk_idx = nullptr;
     int64_t n_mask = 0;
-    // unmasked global ids (any multiplicity), copies ascending: fused update
-    int32_t *un_ptr = nullptr, *un_idx = nullptr;
-    int64_t n_un = 0, n_un_copies = 0;
 
     // CG work vectors and state
     double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr;

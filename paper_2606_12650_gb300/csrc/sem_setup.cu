@@ -249,7 +249,7 @@ int launch_rhs_sin(const Problem *P, const double *verts, double *b) {
 // Copies of one lattice point are grouped by a counting sort over the lattice
 // id; within a group they keep ascending local index (stable fill order).
 struct HostMaps {
-    std::vector<int32_t> sh_ptr, sh_idx, msk_idx, un_ptr, un_idx;
+    std::vector<int32_t> sh_ptr, sh_idx, msk_idx;
     std::vector<double> c;
 };
 
@@ -283,15 +283,10 @@ static void build_maps(int nx, int ny, int nz, int N, HostMaps &M) {
     for (int64_t q = 0; q < nL; ++q) M.c[q] = 1.0 / double(cnt[gid[q]]);
     M.sh_ptr.clear();
     M.sh_idx.clear();
-    M.un_ptr.clear();
-    M.un_idx.clear();
     M.msk_idx.clear();
     M.sh_ptr.reserve(size_t(nG) + 1);
-    M.un_ptr.reserve(size_t(nG) + 1);
     M.sh_idx.reserve(size_t(nL));
-    M.un_idx.reserve(size_t(nL));
     M.sh_ptr.push_back(0);
-    M.un_ptr.push_back(0);
     for (int64_t g = 0; g < nG; ++g) {
         const int64_t gx = g % lx, gy = (g / lx) % ly, gz = g / (lx * ly);
         const bool onb = gx == 0 || gx == lx - 1 || gy == 0 || gy == ly - 1 || gz == 0 || gz == lz - 1;
@@ -300,12 +295,8 @@ static void build_maps(int nx, int ny, int nz, int N, HostMaps &M) {
             for (int64_t q = b0; q < b1; ++q) M.sh_idx.push_back(perm[q]);
             M.sh_ptr.push_back(int32_t(M.sh_idx.size()));
         }
-        if (onb) {
+        if (onb)
             for (int64_t q = b0; q < b1; ++q) M.msk_idx.push_back(perm[q]);
-        } else {
-            for (int64_t q = b0; q < b1; ++q) M.un_idx.push_back(perm[q]);
-            M.un_ptr.push_back(int32_t(M.un_idx.size()));
-        }
     }
     std::sort(M.msk_idx.begin(), M.msk_idx.end());
 }
@@ -387,13 +378,9 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
     if (rc == SEM_OK) {
         P->n_sh = int64_t(M.sh_ptr.size()) - 1;
         P->n_sh_copies = int64_t(M.sh_idx.size());
-        P->n_un = int64_t(M.un_ptr.size()) - 1;
-        P->n_un_copies = int64_t(M.un_idx.size());
         P->n_mask = int64_t(M.msk_idx.size());
         P->sh_ptr = upload(M.sh_ptr, &rc);
         P->sh_idx = upload(M.sh_idx, &rc);
-        P->un_ptr = upload(M.un_ptr, &rc);
-        P->un_idx = upload(M.un_idx, &rc);
         P->msk_idx = upload(M.msk_idx, &rc);
         P->c = upload(M.c, &rc);
     }
@@ -424,7 +411,7 @@ void problem_destroy(Problem *P) {
     double *dptrs[] = {P->verts, P->G, P->B, P->c, P->x, P->r, P->p, P->w, P->partials};
     for (double *q : dptrs)
         if (q) dev_free(q);
-    int32_t *iptrs[] = {P->sh_ptr, P->sh_idx, P->msk_idx, P->un_ptr, P->un_idx};
+    int32_t *iptrs[] = {P->sh_ptr, P->sh_idx, P->msk_idx};
     for (int32_t *q : iptrs)
         if (q) dev_free(q);
     if (P->st) dev_free(P->st);
