@@ -4,63 +4,85 @@
 // (ex, ey, ez) shares its global node with the elements across every element
 // face it lies on: along r when i = 0 (element ex-1, at i = N) or i = N
 // (element ex+1, at i = 0), and likewise along s and t.  Nodes on the cube
-// boundary are Dirichlet (masked).  The copies are listed in ascending local
-// index, which is the (ez, ey, ex) lexicographic order of their elements, so a
-// left-to-right sum over the list adds in the same order as the sorted-segment
-// gather-scatter and gives the same bits at every copy.
+// boundary are Dirichlet (masked).  Moving to the neighbour across the r face
+// changes the local index by sx * (NP - N) (sx = -1 at i = 0, +1 at i = N,
+// NP = (N+1)^3); across s by sy * (nx NP - N (N+1)); across t by
+// sz * (nx ny NP - N (N+1)^2).  Local indices order copies by element first,
+// and element indices are lexicographic in (ez, ey, ex); so visiting the t
+// choice, then s, then r, each with the lower element first, lists the copies
+// in ascending local index -- the order of the sorted-segment gather-scatter,
+// which makes every copy's sum bit-identical.
 #pragma once
 
 #include <cstdint>
 
 namespace sem {
 
-struct BoxCopies {
-    int64_t l[8];   // local indices of the copies, ascending
-    int n;          // number of copies (0 for a masked node)
-    bool owner;     // the node itself is the first copy
+struct BoxNode {
+    int sx, sy, sz;     // -1 low face, +1 high face, 0 interior (per direction)
+    int ox, oy, oz;     // signed local-index offsets to the neighbour copies
+    bool masked;        // on the cube boundary
+    bool owner;         // first copy of its global node
 };
 
 template <int NQ>
-__device__ __forceinline__ BoxCopies box_copies(int64_t node, int nx, int ny, int nz) {
+__device__ __forceinline__ BoxNode box_node(int l, int nx, int ny) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
-    const int64_t e = node / NP;
-    const int q = int(node - e * NP);
+    const unsigned e = unsigned(l) / unsigned(NP);
+    const int q = l - int(e) * NP;
     const int i = q % NQ, j = (q / NQ) % NQ, k = q / NQ2;
-    const int ex = int(e % nx);
-    const int64_t eyz = e / nx;
-    const int ey = int(eyz % ny), ez = int(eyz / ny);
-    BoxCopies out;
-    out.n = 0;
-    out.owner = false;
-    // per direction: the elements sharing the node (ascending) and the node's
-    // index inside each of them
-    int ce[3][2], ci[3][2], cnt[3];
-    const int idx[3] = {i, j, k}, el[3] = {ex, ey, ez}, ne[3] = {nx, ny, nz};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        cnt[d] = 1;
-        ce[d][0] = el[d];
-        ci[d][0] = idx[d];
-        if (idx[d] == 0) {
-            if (el[d] == 0) return out;                 // on the cube boundary: masked
-            ce[d][0] = el[d] - 1; ci[d][0] = N;
-            ce[d][1] = el[d];     ci[d][1] = 0;
-            cnt[d] = 2;
-        } else if (idx[d] == N) {
-            if (el[d] == ne[d] - 1) return out;         // masked
-            ce[d][0] = el[d];     ci[d][0] = N;
-            ce[d][1] = el[d] + 1; ci[d][1] = 0;
-            cnt[d] = 2;
+    const unsigned t = e / unsigned(nx);
+    const int ex = int(e - t * unsigned(nx));
+    const unsigned tz = t / unsigned(ny);
+    const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
+    BoxNode b;
+    b.sx = i == 0 ? -1 : (i == N ? 1 : 0);
+    b.sy = j == 0 ? -1 : (j == N ? 1 : 0);
+    b.sz = k == 0 ? -1 : (k == N ? 1 : 0);
+    b.ox = b.sx * (NP - N);
+    b.oy = b.sy * (nx * NP - N * NQ);
+    b.oz = b.sz * (nx * ny * NP - N * NQ2);
+    return b;
+}
+
+// Completes box_node with the mask and owner flags (needs nz and the element
+// coordinates, recomputed here to keep box_node cheap for callers that only
+// need the offsets).
+template <int NQ>
+__device__ __forceinline__ BoxNode box_node_full(int l, int nx, int ny, int nz) {
+    constexpr int NP = NQ * NQ * NQ;
+    BoxNode b = box_node<NQ>(l, nx, ny);
+    const unsigned e = unsigned(l) / unsigned(NP);
+    const unsigned t = e / unsigned(nx);
+    const int ex = int(e - t * unsigned(nx));
+    const unsigned tz = t / unsigned(ny);
+    const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
+    b.masked = (b.sx < 0 && ex == 0) || (b.sx > 0 && ex == nx - 1) ||
+               (b.sy < 0 && ey == 0) || (b.sy > 0 && ey == ny - 1) ||
+               (b.sz < 0 && ez == 0) || (b.sz > 0 && ez == nz - 1);
+    b.owner = b.sx >= 0 && b.sy >= 0 && b.sz >= 0;
+    return b;
+}
+
+// Sum of v over the copies of node l, in ascending local index.
+template <typename T, typename Acc>
+__device__ __forceinline__ Acc box_sum(const T *__restrict__ v, int l, const BoxNode &b) {
+    const int nzo = b.sz ? 2 : 1, nyo = b.sy ? 2 : 1, nxo = b.sx ? 2 : 1;
+    Acc s = Acc(0);
+    bool first = true;
+    for (int cz = 0; cz < nzo; ++cz) {
+        const int dz = (nzo == 2 && ((b.sz < 0) == (cz == 0))) ? b.oz : 0;
+        for (int cy = 0; cy < nyo; ++cy) {
+            const int dy = (nyo == 2 && ((b.sy < 0) == (cy == 0))) ? b.oy : 0;
+            for (int cx = 0; cx < nxo; ++cx) {
+                const int dx = (nxo == 2 && ((b.sx < 0) == (cx == 0))) ? b.ox : 0;
+                const Acc val = Acc(__ldg(v + l + dz + dy + dx));
+                s = first ? val : s + val;
+                first = false;
+            }
         }
     }
-    out.owner = ce[0][0] == ex && ce[1][0] == ey && ce[2][0] == ez;
-    for (int c = 0; c < cnt[2]; ++c)
-        for (int b = 0; b < cnt[1]; ++b)
-            for (int a = 0; a < cnt[0]; ++a) {
-                const int64_t e2 = ce[0][a] + int64_t(nx) * (ce[1][b] + int64_t(ny) * ce[2][c]);
-                out.l[out.n++] = e2 * NP + ci[0][a] + NQ * (ci[1][b] + NQ * ci[2][c]);
-            }
-    return out;
+    return s;
 }
 
 }  // namespace sem

@@ -166,23 +166,21 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
 template <int NQ>
 __global__ void __launch_bounds__(256) cg_update_box_kernel(double *__restrict__ x, double *__restrict__ r,
                                                             const double *__restrict__ p,
-                                                            const double *__restrict__ w, int64_t nL, int nx,
-                                                            int ny, int nz, double *partials, CgState *st) {
+                                                            const double *__restrict__ w, int nL, int nx, int ny,
+                                                            int nz, double *partials, CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     const double alpha = st->alpha;
     double acc = 0.0;
-    for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < nL;
-         l += int64_t(gridDim.x) * blockDim.x) {
-        const BoxCopies cp = box_copies<NQ>(l, nx, ny, nz);
-        if (cp.n == 0) continue;
-        double ws = __ldg(w + cp.l[0]);
-        for (int c = 1; c < cp.n; ++c) ws += __ldg(w + cp.l[c]);
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x) {
+        const BoxNode b = box_node_full<NQ>(l, nx, ny, nz);
+        if (b.masked) continue;
+        const double ws = box_sum<double, double>(w, l, b);
         const double xn = fma(alpha, p[l], x[l]);
         const double rn = fma(-alpha, ws, r[l]);
         x[l] = xn;
         r[l] = rn;
-        if (cp.owner) acc = fma(rn, rn, acc);
+        if (b.owner) acc = fma(rn, rn, acc);
     }
     const double bs = block_sum(acc, red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
@@ -204,8 +202,8 @@ template <int NQ>
 static int launch_update_nq(const Problem *P) {
     int64_t blocks = (P->nL + kThreads - 1) / kThreads;
     if (blocks > 152 * 64) blocks = 152 * 64;   // grid-stride beyond 9728 blocks
-    cg_update_box_kernel<NQ><<<unsigned(blocks), kThreads, 0, stream()>>>(P->x, P->r, P->p, P->w, P->nL, P->nx,
-                                                                          P->ny, P->nz, P->partials, P->st);
+    cg_update_box_kernel<NQ><<<unsigned(blocks), kThreads, 0, stream()>>>(P->x, P->r, P->p, P->w, int(P->nL),
+                                                                          P->nx, P->ny, P->nz, P->partials, P->st);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "cg_update_box_kernel");
 }
