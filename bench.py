@@ -15,6 +15,9 @@ Also reported on the same JSON line:
                 (pinned b copied in and x copied out every step)
   roofline      the dominant kernel (the fused CG operator kernel) timed with
                 CUDA events on libsem's stream, against the FP64 pipe peak
+  mixed         the same solve by mixed-precision iterative refinement (FP32
+                inner CG, BF16 geometric factors, FP64 outer residual), with
+                its own HBM roofline, solves/s against FP64, and a 1e-10 leg
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
   clocks        nvidia-smi samples taken during the timed region
 
@@ -40,9 +43,10 @@ sys.path.insert(0, ROOT)
 METRIC = "CG GDOF/s to 1e-8 rel. residual, mixed vs FP64 on GB300; serve p50/p99 ms"
 # FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (max SM clock) = 1.259 TFLOP/s
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
-              for f in ("sem_ax.cu", "sem_device.cuh", "sem_internal.h")]
+              for f in ("sem_ax_kernel.cuh", "sem_ax.cu", "sem_device.cuh", "sem_internal.h")]
 
 
 def parse():
@@ -59,6 +63,8 @@ def parse():
     ap.add_argument("--cpu-iters", type=int, default=10, help="oracle CG iterations per CPU sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--inner-tol", type=float, default=1e-3, help="inner FP32 CG residual reduction")
     return ap.parse_args()
 
 
@@ -266,12 +272,17 @@ def run_ours(a):
         pass
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "kernel": f"ax_f64_kernel<{N + 1},2,CG>", "launch_ms": ax_ms,
+                "kernel": f"ax_kernel<{N + 1},2,double,double,CG>", "launch_ms": ax_ms,
                 "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
                 "hbm_gbs_at_alg_bytes": bytes_alg / (ax_ms * 1e-3) / 1e9,
                 "fp64_probe_gflops": fp64.value / 1e9,
                 "peak_note": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 2 DFMA/clk x "
                              "2 flop x 2.07 GHz); fp64_probe_gflops is the same pipe measured live"}
+
+    # ---- mixed precision: FP32 inner CG (BF16 geometric factors), FP64 refinement
+    mixed = None
+    if not a.no_mixed:
+        mixed = run_mixed(a, M, b, x, t_max, world, barrier, stream, sem, torch, dist)
 
     # ---- end to end through the public API, host buffers
     e2e = None
@@ -324,6 +335,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "mixed": mixed,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
@@ -333,6 +345,83 @@ def run_ours(a):
     sem.finalize()
     if world > 1:
         dist.destroy_process_group()
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def run_mixed(a, M, b, x64, t64_ms, world, barrier, stream, sem, torch, dist):
+    """Same problem and tolerance through mixed-precision refinement; also a
+    1e-10 solve (FP64 CG and mixed) for the error table."""
+    E, N = a.nx ** 3, a.N
+    xm = torch.empty_like(b)
+    for _ in range(a.warmup):
+        M.cg_mixed(b, xm, a.tol, 50, a.inner_tol, a.maxit, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    inner_tot, outer, res = 0, 0, 0.0
+    ev0.record(stream)
+    for _ in range(a.steps):
+        inner, outer, res = M.cg_mixed(b, xm, a.tol, 50, a.inner_tol, a.maxit, 1)
+        inner_tot += inner
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_ms = ev0.elapsed_time(ev1)
+    dofs = float(E * N ** 3 * inner_tot)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
+        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+        dofs = float(dd.item())
+    err_vs_fp64 = float((xm - x64).abs().max().item() / x64.abs().max().item())
+    true_res = M.true_res(b, xm)
+    # inner operator kernel (FP32, BF16 G), timed alone on libsem's stream
+    for _ in range(3):
+        sem.run("cg_ax32", M.handle, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.ax_reps):
+        sem.run("cg_ax32", M.handle, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ax_ms = e0.elapsed_time(e1) / a.ax_reps
+    alg = E * (N + 1) ** 3 * 28   # r, p in (FP32); p, w out (FP32); 6 BF16 factors
+    peak, how = hbm_peak()
+    gbs = alg / (ax_ms * 1e-3) / 1e9
+    # 1e-10: FP64 CG reference and mixed refinement
+    x10 = torch.empty_like(b)
+    t0 = time.perf_counter()
+    it10, _ = M.cg_solve(b, x10, 1e-10, a.maxit)
+    t_fp64_10 = time.perf_counter() - t0
+    xm10 = torch.empty_like(b)
+    t0 = time.perf_counter()
+    in10, out10, res10 = M.cg_mixed(b, xm10, 1e-10, 50, a.inner_tol, a.maxit, 1)
+    t_mix_10 = time.perf_counter() - t0
+    err10 = float((xm10 - x10).abs().max().item() / x10.abs().max().item())
+    return {"metric": METRIC, "value": dofs / (t_ms * 1e-3) / 1e9, "unit": "GDOF/s",
+            "gdofs_counts": "inner FP32 CG iterations (E N^3 per iteration)",
+            "dtype": "f32 inner CG, bf16 geometric factors, f64 refinement/dots/alpha/beta",
+            "workload": f"same problem, mixed-precision refinement to {a.tol:g} (inner tolerance {a.inner_tol:g})",
+            "ms_per_solve": t_ms / a.steps, "solves_per_s": 1e3 * a.steps / t_ms * world,
+            "fp64_solves_per_s": 1e3 * a.steps / t64_ms * world,
+            "speedup_solves_vs_fp64": t64_ms / t_ms,
+            "inner_iters_per_solve": inner_tot // max(a.steps, 1), "outer_iters": outer,
+            "rel_res_true": true_res, "err_vs_fp64_cg_inf": err_vs_fp64,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None, "kernel": f"ax_kernel<{N + 1},4,float,bf16,CG>",
+                         "launch_ms": ax_ms, "alg_bytes_per_launch": alg, "peak_source": how},
+            "tol_1e-10": {"fp64_cg_iters": it10, "fp64_ms": 1e3 * t_fp64_10,
+                          "mixed_inner_iters": in10, "mixed_outer_iters": out10, "mixed_ms": 1e3 * t_mix_10,
+                          "mixed_rel_res_true": res10, "err_vs_fp64_cg_inf": err10}}
 
 
 def main():

@@ -138,6 +138,23 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               maxit).  rho = <r,r>_c.  hist (maxit+1 doubles, optional)
  *               receives sqrt(rho_k).  rel_res = sqrt(rho/rho_0) at exit.
  *   "true_res"  handle, b, x, OUT d     ||b - A x||_c / ||b||_c (FP64)
+ *   "ax32"      handle, x, y, gprec     y = A_local x in FP32 (x, y: nL floats);
+ *                                       geometric factors rounded to nearest
+ *                                       even from FP64 to FP32 (gprec 0) or
+ *                                       BF16 (gprec 1), converted once per problem
+ *   "cg_ax32"   handle, gprec           one launch of the inner (FP32) CG operator
+ *                                       kernel on the problem's FP32 vectors, stop
+ *                                       flag cleared; for timing after cg_mixed
+ *   "cg_mixed"  handle, b, x, tol, max_outer, inner_tol, inner_maxit, gprec,
+ *               OUT inner_iters, OUT outer_iters, OUT rel_res, [hist_outer]
+ *               Mixed-precision iterative refinement: from x = 0 the FP64
+ *               residual r = b - A x is recomputed after each inner CG solve
+ *               of A d = r run in FP32 (FP32 vectors and arithmetic, G in FP32
+ *               or BF16, dot sums, alpha and beta in FP64) until its residual
+ *               fell by max(inner_tol, 0.5 tol/||r||) (relative), and x += d
+ *               in FP64; stops when ||b - A x||_c/||b||_c <= tol or after
+ *               max_outer corrections.  rel_res is that true residual;
+ *               hist_outer (max_outer+1 doubles) its value before each step.
  *   "cg_ax"     handle                  one launch of the CG iteration's fused
  *                                       operator kernel on the problem's own CG
  *                                       vectors (p = r + beta p, w = A_local p,

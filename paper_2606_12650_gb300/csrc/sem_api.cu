@@ -410,6 +410,56 @@ int run_cg_solve(ArgReader &R) {
     return cg_solve(P, b, x, tol, int(maxit), hist, oit, ores);
 }
 
+int run_ax32(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(float);
+    const float *x = static_cast<const float *>(R.arr(1, vb, "x"));
+    float *y = static_cast<float *>(R.arr(2, vb, "y"));
+    const int64_t gprec = R.i(3, "gprec");
+    if (R.err) return R.err;
+    if (x == y) return R.fail(SEM_EARG, "x and y must not alias");
+    const int rc = mixed_prepare(P, int(gprec));
+    return rc != SEM_OK ? rc : launch_ax32(P, x, y, int(gprec));
+}
+
+int run_cg_ax32(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    Problem *P = get_problem(R, 0);
+    const int64_t gprec = R.i(1, "gprec");
+    if (R.err) return R.err;
+    int rc = mixed_prepare(P, int(gprec));
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemsetAsync(&P->st_in->done, 0, sizeof(int32_t), g.cur_stream), "cg_ax32: flag");
+    return rc != SEM_OK ? rc : launch_ax32_cg(P, int(gprec));
+}
+
+int run_cg_mixed(ArgReader &R) {
+    if (!R.need(11)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b"));
+    double *x = static_cast<double *>(R.arr(2, vb, "x"));
+    const double tol = R.d(3, "tol");
+    const int64_t max_outer = R.i(4, "max_outer");
+    const double inner_tol = R.d(5, "inner_tol");
+    const int64_t inner_maxit = R.i(6, "inner_maxit");
+    const int64_t gprec = R.i(7, "gprec");
+    int64_t *o_in = static_cast<int64_t *>(R.out(8, SEM_ARG_OUT_INT, "inner_iters"));
+    int64_t *o_out = static_cast<int64_t *>(R.out(9, SEM_ARG_OUT_INT, "outer_iters"));
+    double *o_res = static_cast<double *>(R.out(10, SEM_ARG_OUT_DOUBLE, "rel_res"));
+    if (R.err) return R.err;
+    if (max_outer < 0 || max_outer > 1000 || inner_maxit < 1 || inner_maxit > (1 << 30))
+        return R.fail(SEM_EARG, "max_outer must be in [0, 1000] and inner_maxit in [1, 2^30]");
+    double *hist = static_cast<double *>(R.arr(11, size_t(max_outer + 1) * sizeof(double), "hist_outer", true));
+    if (R.err) return R.err;
+    if (b == x) return R.fail(SEM_EARG, "b and x must not alias");
+    return mixed_solve(P, b, x, tol, int(max_outer), inner_tol, int(inner_maxit), int(gprec), o_in, o_out, o_res,
+                       hist);
+}
+
 int run_cg_ax(ArgReader &R) {
     if (!R.need(1)) return R.err;
     Problem *P = get_problem(R, 0);
@@ -584,6 +634,9 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "cg_solve") rc = run_cg_solve(R);
     else if (k == "true_res") rc = run_true_res(R);
     else if (k == "cg_ax") rc = run_cg_ax(R);
+    else if (k == "ax32") rc = run_ax32(R);
+    else if (k == "cg_ax32") rc = run_cg_ax32(R);
+    else if (k == "cg_mixed") rc = run_cg_mixed(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
     else return set_error(SEM_EKERNEL, "sem_run: unknown kernel '" + k + "'");
     return rc;

@@ -26,7 +26,7 @@ struct BoxNode {
 };
 
 template <int NQ>
-__device__ __forceinline__ BoxNode box_node(int l, int nx, int ny) {
+__device__ __forceinline__ BoxNode box_node(int l, int nx, int ny, int nz) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
     const unsigned e = unsigned(l) / unsigned(NP);
     const int q = l - int(e) * NP;
@@ -42,21 +42,6 @@ __device__ __forceinline__ BoxNode box_node(int l, int nx, int ny) {
     b.ox = b.sx * (NP - N);
     b.oy = b.sy * (nx * NP - N * NQ);
     b.oz = b.sz * (nx * ny * NP - N * NQ2);
-    return b;
-}
-
-// Completes box_node with the mask and owner flags (needs nz and the element
-// coordinates, recomputed here to keep box_node cheap for callers that only
-// need the offsets).
-template <int NQ>
-__device__ __forceinline__ BoxNode box_node_full(int l, int nx, int ny, int nz) {
-    constexpr int NP = NQ * NQ * NQ;
-    BoxNode b = box_node<NQ>(l, nx, ny);
-    const unsigned e = unsigned(l) / unsigned(NP);
-    const unsigned t = e / unsigned(nx);
-    const int ex = int(e - t * unsigned(nx));
-    const unsigned tz = t / unsigned(ny);
-    const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
     b.masked = (b.sx < 0 && ex == 0) || (b.sx > 0 && ex == nx - 1) ||
                (b.sy < 0 && ey == 0) || (b.sy > 0 && ey == ny - 1) ||
                (b.sz < 0 && ez == 0) || (b.sz > 0 && ez == nz - 1);

@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) cg_update_box_kernel(double *__restrict__
     const double alpha = st->alpha;
     double acc = 0.0;
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x) {
-        const BoxNode b = box_node_full<NQ>(l, nx, ny, nz);
+        const BoxNode b = box_node<NQ>(l, nx, ny, nz);
         if (b.masked) continue;
         const double ws = box_sum<double, double>(w, l, b);
         const double xn = fma(alpha, p[l], x[l]);
@@ -185,16 +185,7 @@ __global__ void __launch_bounds__(256) cg_update_box_kernel(double *__restrict__
     const double bs = block_sum(acc, red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
-        if (threadIdx.x == 0) {
-            const int it = st->iter + 1;
-            st->iter = it;
-            if (st->hist) st->hist[it] = sqrt(rho_new);
-            const double rho = st->rho;
-            st->beta = rho_new / rho;
-            st->rho = rho_new;
-            const bool conv = st->tol > 0.0 && sqrt(rho_new / st->rho0) <= st->tol;
-            if (conv || it >= st->maxit) st->done = 1;
-        }
+        if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
     }
 }
 

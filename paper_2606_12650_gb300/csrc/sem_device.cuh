@@ -172,4 +172,18 @@ __device__ __forceinline__ double finish_partials(const double *partials, int n,
     return acc;
 }
 
+// Closing step of a CG iteration, run by thread 0 of the last block once
+// rho_new = <r_{k+1}, r_{k+1}> is known: iteration count, optional history,
+// beta = rho_new / rho, and the stop flag (relative residual or maxit).
+__device__ __forceinline__ void cg_close_iteration(CgState *st, double rho_new) {
+    const int it = st->iter + 1;
+    st->iter = it;
+    if (st->hist) st->hist[it] = sqrt(rho_new);
+    const double rho = st->rho;
+    st->beta = rho_new / rho;
+    st->rho = rho_new;
+    const bool conv = st->tol > 0.0 && sqrt(rho_new / st->rho0) <= st->tol;
+    if (conv || it >= st->maxit) st->done = 1;
+}
+
 }  // namespace sem

@@ -77,7 +77,21 @@ struct Problem {
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;
+
+    // mixed precision (allocated on first use): geometric factors rounded to
+    // FP32 or BF16 ([nL][6]), FP32 inner-CG vectors and the inner CG state
+    void *G32 = nullptr;           // float
+    void *G16 = nullptr;           // __nv_bfloat16
+    float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *w32 = nullptr;
+    CgState *st_in = nullptr;
+    CgState *st_in_host = nullptr;
+    cudaGraphExec_t graph32[2] = {nullptr, nullptr};  // per geometric-factor precision
+    int graph32_iters = 0;
+    cudaStream_t graph32_stream = nullptr;
 };
+
+// storage precision of the geometric factors in mixed-precision inner solves
+enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
 
 // ---- runtime services (sem_api.cu) ---------------------------------------
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
@@ -101,6 +115,15 @@ int launch_scale(const Problem *P, const double *a, const double *f, double *out
 int prepare_ax(const Problem *P);             // kernel attributes (before any capture)
 int launch_ax(const Problem *P, const double *x, double *y);
 int launch_ax_cg(const Problem *P);          // p = r + beta p; w = A_local p; <p,w>
+int prepare_ax32(const Problem *P);
+int convert_geometry(const Problem *P, int gprec, void *out);
+int launch_ax32(const Problem *P, const float *x, float *y, int gprec);
+int launch_ax32_cg(const Problem *P, int gprec);   // inner CG on r32/p32/w32 with st_in
+int mixed_prepare(Problem *P, int gprec);          // allocate + convert on first use
+int mixed_solve(Problem *P, const double *b, double *x, double tol, int max_outer, double inner_tol,
+                int inner_maxit, int gprec, int64_t *inner_iters, int64_t *outer_iters, double *rel_res,
+                double *hist_outer);
+void mixed_release(Problem *P);
 int launch_gs(const Problem *P, double *u);
 int launch_mask(const Problem *P, double *u);
 int launch_dot(const Problem *P, const double *u, const double *v);  // -> st->dot_out

@@ -70,6 +70,19 @@ class Mesh:
         sem.run("cg_solve", self.handle, b, x, float(tol), int(maxit), it, res, hist)
         return it.value, res.value
 
+    def ax32(self, x, y, gprec: int = 1):
+        """y = A_local x in FP32 with G stored FP32 (gprec 0) or BF16 (gprec 1)."""
+        sem.run("ax32", self.handle, x, y, int(gprec))
+
+    def cg_mixed(self, b, x, tol: float, max_outer: int = 50, inner_tol: float = 1e-3,
+                 inner_maxit: int = 100000, gprec: int = 1, hist_outer=None):
+        """Mixed-precision iterative refinement; returns (inner_iters, outer_iters,
+        true relative residual)."""
+        i, o, r = sem.OutInt(), sem.OutInt(), sem.OutDouble()
+        sem.run("cg_mixed", self.handle, b, x, float(tol), int(max_outer), float(inner_tol),
+                int(inner_maxit), int(gprec), i, o, r, hist_outer)
+        return i.value, o.value, r.value
+
     def true_res(self, b, x) -> float:
         o = sem.OutDouble()
         sem.run("true_res", self.handle, b, x, o)
