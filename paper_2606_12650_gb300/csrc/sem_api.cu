@@ -108,6 +108,7 @@ void dev_free(void *p) {
 }
 
 cudaStream_t stream() { return g.cur_stream; }
+int sm_count() { return g.prop.multiProcessorCount > 0 ? g.prop.multiProcessorCount : 1; }
 int32_t *status_word() { return g.status_dev; }
 int32_t *status_host() { return g.status_pinned; }
 void count_launches(int64_t n) { g_launches += n; }

@@ -11,11 +11,11 @@
 // CG (Nekbone without preconditioner, Section VIII-A).  One iteration is two
 // kernels:
 //   1. ax_f64_kernel<CG>: p = r + beta p; w = A_local p; <p, A p>; alpha
-//   2. cg_update_box_kernel: every local node sums the copies of w of its
-//      global node in ascending local index (the direct-stiffness sum), then
-//      applies x += alpha p and r -= alpha (QQ^T w) to itself; <r, r> is
-//      accumulated once per global node; the last block forms rho, beta, the
-//      iteration count and the stop flag.
+//   2. cg_update_rows_kernel (sem_box.cuh): every local node sums the copies
+//      of w of its global node in ascending local index (the direct-stiffness
+//      sum), then applies x += alpha p and r -= alpha (QQ^T w) to itself;
+//      <r, r> is accumulated once per global node; the last block forms rho,
+//      beta, the iteration count and the stop flag.
 // The dot products of the paper are tree reductions (Section VIII-B, the
 // unrolled reduction of Table "HIP-variable vs HIP-fixed"); here each block
 // reduces in a fixed order and the last block to finish sums the per-block
@@ -157,61 +157,8 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
     return cuda_check(cudaGetLastError(), "cg_init_kernel");
 }
 
-// Fused direct-stiffness sum + CG update, one thread per local node in the
-// natural (coalesced) order.  Every copy of a global node adds all copies of
-// w in ascending local index (same bits at each copy), then updates its own
-// x and r; x, p and r are continuous, so every copy computes the same values.
-// <r, r> counts each global node once, at its first copy.  Masked nodes are
-// left at zero.
-template <int NQ>
-__global__ void __launch_bounds__(256) cg_update_box_kernel(double *__restrict__ x, double *__restrict__ r,
-                                                            const double *__restrict__ p,
-                                                            const double *__restrict__ w, int nL, int nx, int ny,
-                                                            int nz, double *partials, CgState *st) {
-    __shared__ double red[32];
-    if (st->done) return;
-    const double alpha = st->alpha;
-    double acc = 0.0;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x) {
-        const BoxNode b = box_node<NQ>(l, nx, ny, nz);
-        if (b.masked) continue;
-        const double ws = box_sum<double, double>(w, l, b);
-        const double xn = fma(alpha, p[l], x[l]);
-        const double rn = fma(-alpha, ws, r[l]);
-        x[l] = xn;
-        r[l] = rn;
-        if (b.owner) acc = fma(rn, rn, acc);
-    }
-    const double bs = block_sum(acc, red);
-    if (publish_partial(bs, partials, &st->ticket_up)) {
-        const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
-        if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
-    }
-}
-
-template <int NQ>
-static int launch_update_nq(const Problem *P) {
-    int64_t blocks = (P->nL + kThreads - 1) / kThreads;
-    if (blocks > 152 * 64) blocks = 152 * 64;   // grid-stride beyond 9728 blocks
-    cg_update_box_kernel<NQ><<<unsigned(blocks), kThreads, 0, stream()>>>(P->x, P->r, P->p, P->w, int(P->nL),
-                                                                          P->nx, P->ny, P->nz, P->partials, P->st);
-    count_launches(1);
-    return cuda_check(cudaGetLastError(), "cg_update_box_kernel");
-}
-
 int launch_cg_update(const Problem *P) {
-    switch (P->nq) {
-        case 2: return launch_update_nq<2>(P);
-        case 3: return launch_update_nq<3>(P);
-        case 4: return launch_update_nq<4>(P);
-        case 5: return launch_update_nq<5>(P);
-        case 6: return launch_update_nq<6>(P);
-        case 7: return launch_update_nq<7>(P);
-        case 8: return launch_update_nq<8>(P);
-        case 9: return launch_update_nq<9>(P);
-        case 10: return launch_update_nq<10>(P);
-        default: return set_error(SEM_EARG, "cg: unsupported order");
-    }
+    return launch_update_rows<double, double>(P, P->x, P->r, P->p, P->w, P->st);
 }
 
 // Iterations per captured graph: the host polls the stop flag once per replay.

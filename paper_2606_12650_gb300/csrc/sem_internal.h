@@ -97,6 +97,7 @@ enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
 void dev_free(void *p);
 cudaStream_t stream();
+int sm_count();                    // SMs of the current device
 int32_t *status_word();            // device status word (kernels write it)
 int32_t *status_host();            // pinned host copy (filled by poll_status / cg_solve)
 int poll_status();                 // sync, read and clear the status word -> SEM_OK/SEM_ETIMEDOUT

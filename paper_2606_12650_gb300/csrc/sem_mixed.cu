@@ -65,56 +65,8 @@ __global__ void mixed_correct_kernel(double *__restrict__ x, const float *__rest
     if (l < n) x[l] += double(d[l]);
 }
 
-// FP32 twin of cg_update_box_kernel: gather-scatter of w fused with the inner
-// update; per-thread partials in FP32, block and grid sums in FP64.
-template <int NQ>
-__global__ void __launch_bounds__(256) cg_update_box_f32_kernel(float *__restrict__ x, float *__restrict__ r,
-                                                                const float *__restrict__ p,
-                                                                const float *__restrict__ w, int nL, int nx,
-                                                                int ny, int nz, double *partials, CgState *st) {
-    __shared__ double red[32];
-    if (st->done) return;
-    const float alpha = float(st->alpha);
-    float acc = 0.f;
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x) {
-        const BoxNode b = box_node<NQ>(l, nx, ny, nz);
-        if (b.masked) continue;
-        const float ws = box_sum<float, float>(w, l, b);
-        x[l] = fmaf(alpha, p[l], x[l]);
-        const float rn = fmaf(-alpha, ws, r[l]);
-        r[l] = rn;
-        if (b.owner) acc = fmaf(rn, rn, acc);
-    }
-    const double bs = block_sum(double(acc), red);
-    if (publish_partial(bs, partials, &st->ticket_up)) {
-        const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
-        if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
-    }
-}
-
-template <int NQ>
-static int launch_update32_nq(const Problem *P) {
-    int64_t blocks = (P->nL + kThreads32 - 1) / kThreads32;
-    if (blocks > 152 * 64) blocks = 152 * 64;
-    cg_update_box_f32_kernel<NQ><<<unsigned(blocks), kThreads32, 0, stream()>>>(
-        P->d32, P->r32, P->p32, P->w32, int(P->nL), P->nx, P->ny, P->nz, P->partials, P->st_in);
-    count_launches(1);
-    return cuda_check(cudaGetLastError(), "cg_update_box_f32_kernel");
-}
-
 static int launch_update32(const Problem *P) {
-    switch (P->nq) {
-        case 2: return launch_update32_nq<2>(P);
-        case 3: return launch_update32_nq<3>(P);
-        case 4: return launch_update32_nq<4>(P);
-        case 5: return launch_update32_nq<5>(P);
-        case 6: return launch_update32_nq<6>(P);
-        case 7: return launch_update32_nq<7>(P);
-        case 8: return launch_update32_nq<8>(P);
-        case 9: return launch_update32_nq<9>(P);
-        case 10: return launch_update32_nq<10>(P);
-        default: return set_error(SEM_EARG, "mixed: unsupported order");
-    }
+    return launch_update_rows<float, float>(P, P->d32, P->r32, P->p32, P->w32, P->st_in);
 }
 
 int mixed_prepare(Problem *P, int gprec) {
