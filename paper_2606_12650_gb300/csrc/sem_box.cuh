@@ -49,102 +49,48 @@ __device__ __forceinline__ BoxNode box_node(int l, int nx, int ny, int nz) {
     return b;
 }
 
-// Sum of v over the copies of node l, in ascending local index.
-template <typename T, typename Acc>
-__device__ __forceinline__ Acc box_sum(const T *__restrict__ v, int l, const BoxNode &b) {
-    const int nzo = b.sz ? 2 : 1, nyo = b.sy ? 2 : 1, nxo = b.sx ? 2 : 1;
-    Acc s = Acc(0);
-    bool first = true;
-    for (int cz = 0; cz < nzo; ++cz) {
-        const int dz = (nzo == 2 && ((b.sz < 0) == (cz == 0))) ? b.oz : 0;
-        for (int cy = 0; cy < nyo; ++cy) {
-            const int dy = (nyo == 2 && ((b.sy < 0) == (cy == 0))) ? b.oy : 0;
-            for (int cx = 0; cx < nxo; ++cx) {
-                const int dx = (nxo == 2 && ((b.sx < 0) == (cx == 0))) ? b.ox : 0;
-                const Acc val = Acc(__ldg(v + l + dz + dy + dx));
-                s = first ? val : s + val;
-                first = false;
-            }
-        }
-    }
-    return s;
-}
-
 }  // namespace sem
 
 namespace sem {
 
-// Fused direct-stiffness sum + CG update over element rows.  A row is the
-// NQ nodes (i = 0..N) of one (j, k) line of one element: contiguous in
-// memory, so a warp's rows form one contiguous run.  For a row, the copies of
-// its nodes across the s and t faces are whole rows of the neighbouring
-// elements (loaded as rows); only the two end nodes also have copies across
-// the r faces (single values).  Every copy of a node sums the same list in
-// ascending local index, so all copies get the same bits; each copy updates
-// only itself:  x += alpha p,  r -= alpha (QQ^T w).  Masked nodes are left
-// unchanged (they stay zero).  Returns this thread's partial of <r, r> over
-// the rows it owns (each global node counted at its first copy).
+// Fused direct-stiffness sum + CG update for one local node l.  The node's
+// copies are the combinations of {own, neighbour} element along each
+// direction in which it lies on an interior element face; enumerating
+// (t, s, r) choices with the lower element first lists them in ascending
+// local index.  All candidate loads are issued straight-line (predicated), so
+// they are independent; the sum then runs left to right over the valid ones,
+// which gives every copy of the node the same bits.  The node then updates
+// itself: x += alpha p, r -= alpha (QQ^T w).  Masked nodes are left as they
+// are (zero).  Returns the node's contribution to <r, r> (at its first copy).
 template <int NQ, typename T, typename Acc>
-__device__ __forceinline__ Acc update_row(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                         const T *__restrict__ w, int row, int nx, int ny, int nz, T alpha) {
-    constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
-    const unsigned e = unsigned(row) / unsigned(NQ2);
-    const int jk = row - int(e) * NQ2;
-    const int j = jk % NQ, k = jk / NQ;
-    const unsigned t = e / unsigned(nx);
-    const int ex = int(e - t * unsigned(nx));
-    const unsigned tz = t / unsigned(ny);
-    const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
-    const int sy = j == 0 ? -1 : (j == N ? 1 : 0);
-    const int sz = k == 0 ? -1 : (k == N ? 1 : 0);
-    if ((sy < 0 && ey == 0) || (sy > 0 && ey == ny - 1) || (sz < 0 && ez == 0) || (sz > 0 && ez == nz - 1))
-        return Acc(0);                                   // the whole row is on the cube boundary
-    const int base = row * NQ;
-    const int oy = sy * (nx * NP - N * NQ);
-    const int oz = sz * (nx * ny * NP - N * NQ2);
-    const bool xlo = ex > 0, xhi = ex < nx - 1;          // r-face neighbours exist
-    const int nzo = sz ? 2 : 1, nyo = sy ? 2 : 1;
-    // Copies across the t and s faces are whole rows; visit the (t, s)
-    // choices in ascending element order (t major, lower element first) and
-    // accumulate every node's sum in place.
-    Acc ws[NQ];
+__device__ __forceinline__ Acc update_node(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                                          const T *__restrict__ w, int l, int nx, int ny, int nz, T alpha) {
+    const BoxNode b = box_node<NQ>(l, nx, ny, nz);
+    if (b.masked) return Acc(0);
+    // per direction: offset of option 0 (the lower element) and option 1
+    const int z0 = b.sz < 0 ? b.oz : 0, z1 = b.sz > 0 ? b.oz : 0;
+    const int y0 = b.sy < 0 ? b.oy : 0, y1 = b.sy > 0 ? b.oy : 0;
+    const int x0 = b.sx < 0 ? b.ox : 0, x1 = b.sx > 0 ? b.ox : 0;
+    T v[8];
 #pragma unroll
-    for (int i = 0; i < NQ; ++i) ws[i] = Acc(0);
-    bool first = true;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int cz = c >> 1, cy = c & 1;
-        if (cz >= nzo || cy >= nyo) continue;
-        const int dz = (nzo == 2 && ((sz < 0) == (cz == 0))) ? oz : 0;
-        const int dy = (nyo == 2 && ((sy < 0) == (cy == 0))) ? oy : 0;
-        const T *wc = w + base + dz + dy;
-        const Acc lo = xlo ? Acc(__ldg(wc - (NP - N))) : Acc(0);   // element ex-1, node i = N
-        const Acc hi = xhi ? Acc(__ldg(wc + NP)) : Acc(0);         // element ex+1, node i = 0
-#pragma unroll
-        for (int i = 0; i < NQ; ++i) {
-            const Acc v = Acc(__ldg(wc + i));
-            Acc s = ws[i];
-            if (i == 0 && xlo) s = first ? lo : s + lo;
-            s = (first && !(i == 0 && xlo)) ? v : s + v;
-            if (i == N && xhi) s = s + hi;
-            ws[i] = s;
-        }
-        first = false;
+    for (int c = 0; c < 8; ++c) {
+        const int cz = c >> 2, cy = (c >> 1) & 1, cx = c & 1;
+        const bool valid = (cz == 0 || b.sz) && (cy == 0 || b.sy) && (cx == 0 || b.sx);
+        const int off = (cz ? z1 : z0) + (cy ? y1 : y0) + (cx ? x1 : x0);
+        v[c] = valid ? __ldg(w + l + off) : T(0);
     }
-    const bool owner_row = sy >= 0 && sz >= 0;
-    Acc acc = Acc(0);
+    Acc s = Acc(v[0]);
 #pragma unroll
-    for (int i = 0; i < NQ; ++i) {
-        const bool masked = (i == 0 && !xlo) || (i == N && !xhi);
-        if (masked) continue;
-        const T xn = fma(alpha, p[base + i], x[base + i]);
-        const T rn = fma(-alpha, T(ws[i]), r[base + i]);
-        x[base + i] = xn;
-        r[base + i] = rn;
-        const bool owner = owner_row && !(i == 0 && xlo);
-        if (owner) acc = fma(Acc(rn), Acc(rn), acc);
+    for (int c = 1; c < 8; ++c) {
+        const int cz = c >> 2, cy = (c >> 1) & 1, cx = c & 1;
+        const bool valid = (cz == 0 || b.sz) && (cy == 0 || b.sy) && (cx == 0 || b.sx);
+        if (valid) s = s + Acc(v[c]);
     }
-    return acc;
+    const T xn = fma(alpha, p[l], x[l]);
+    const T rn = fma(-alpha, T(s), r[l]);
+    x[l] = xn;
+    r[l] = rn;
+    return b.owner ? Acc(rn) * Acc(rn) : Acc(0);
 }
 
 }  // namespace sem
@@ -153,20 +99,20 @@ __device__ __forceinline__ Acc update_row(T *__restrict__ x, T *__restrict__ r, 
 
 namespace sem {
 
-// One CG update step over all element rows (grid-stride), with the <r, r>
+// One CG update step over all local nodes (grid-stride), with the <r, r>
 // reduction: per-thread partials in Acc, block and grid sums in FP64, and the
 // last block closes the iteration (beta, counter, stop flag).
 template <int NQ, typename T, typename Acc>
-__global__ void __launch_bounds__(256) cg_update_rows_kernel(T *__restrict__ x, T *__restrict__ r,
-                                                             const T *__restrict__ p, const T *__restrict__ w,
-                                                             int nrows, int nx, int ny, int nz, double *partials,
-                                                             CgState *st) {
+__global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x, T *__restrict__ r,
+                                                              const T *__restrict__ p, const T *__restrict__ w,
+                                                              int nL, int nx, int ny, int nz, double *partials,
+                                                              CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     const T alpha = T(st->alpha);
     Acc acc = Acc(0);
-    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < nrows; row += gridDim.x * blockDim.x)
-        acc += update_row<NQ, T, Acc>(x, r, p, w, row, nx, ny, nz, alpha);
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x)
+        acc += update_node<NQ, T, Acc>(x, r, p, w, l, nx, ny, nz, alpha);
     const double bs = block_sum(double(acc), red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
@@ -176,13 +122,12 @@ __global__ void __launch_bounds__(256) cg_update_rows_kernel(T *__restrict__ x, 
 
 template <int NQ, typename T, typename Acc>
 static int launch_update_rows_nq(const Problem *P, T *x, T *r, const T *p, const T *w, CgState *st) {
-    const int64_t nrows = P->E * NQ * NQ;
-    int64_t blocks = (nrows + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~7 rows per thread at E = 32768, N = 7
-    cg_update_rows_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(nrows), P->nx, P->ny,
-                                                                              P->nz, P->partials, st);
+    int64_t blocks = (P->nL + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~54 nodes per thread at E = 32768, N = 7
+    cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(P->nL), P->nx,
+                                                                               P->ny, P->nz, P->partials, st);
     count_launches(1);
-    return cuda_check(cudaGetLastError(), "cg_update_rows_kernel");
+    return cuda_check(cudaGetLastError(), "cg_update_nodes_kernel");
 }
 
 template <typename T, typename Acc>

@@ -11,7 +11,7 @@
 // CG (Nekbone without preconditioner, Section VIII-A).  One iteration is two
 // kernels:
 //   1. ax_f64_kernel<CG>: p = r + beta p; w = A_local p; <p, A p>; alpha
-//   2. cg_update_rows_kernel (sem_box.cuh): every local node sums the copies
+//   2. cg_update_nodes_kernel (sem_box.cuh): every local node sums the copies
 //      of w of its global node in ascending local index (the direct-stiffness
 //      sum), then applies x += alpha p and r -= alpha (QQ^T w) to itself;
 //      <r, r> is accumulated once per global node; the last block forms rho,
