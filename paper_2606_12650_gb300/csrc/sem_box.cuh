@@ -99,6 +99,123 @@ __device__ __forceinline__ Acc update_node(T *__restrict__ x, T *__restrict__ r,
 
 namespace sem {
 
+// Vector width for the update: V consecutive nodes of one row share the
+// element, j and k; V divides N+1 and V * sizeof(T) <= 16 bytes.
+template <int NQ, typename T>
+struct UpdVec {
+    static constexpr int by16 = 16 / int(sizeof(T));
+    static constexpr int value = (NQ % by16 == 0) ? by16 : ((NQ % 2 == 0 && by16 >= 2) ? 2 : 1);
+};
+
+template <typename T, int V>
+struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 2> { using type = float2; };
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <> struct VecT<double, 1> { using type = double; };
+
+template <typename T, int V>
+__device__ __forceinline__ void vload(const T *p, T (&v)[V]) {
+    const typename VecT<T, V>::type q = *reinterpret_cast<const typename VecT<T, V>::type *>(p);
+    const T *a = reinterpret_cast<const T *>(&q);
+#pragma unroll
+    for (int c = 0; c < V; ++c) v[c] = a[c];
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vload_nc(const T *p, T (&v)[V]) {
+    const typename VecT<T, V>::type q = __ldg(reinterpret_cast<const typename VecT<T, V>::type *>(p));
+    const T *a = reinterpret_cast<const T *>(&q);
+#pragma unroll
+    for (int c = 0; c < V; ++c) v[c] = a[c];
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
+    typename VecT<T, V>::type q;
+    T *a = reinterpret_cast<T *>(&q);
+#pragma unroll
+    for (int c = 0; c < V; ++c) a[c] = v[c];
+    *reinterpret_cast<typename VecT<T, V>::type *>(p) = q;
+}
+
+// Fused gs + update for the V consecutive nodes l0 .. l0+V-1 (one row piece).
+// Same sums as update_node: for each (t, s) choice in ascending element
+// order, the r-face neighbour (node i = 0 only, lower element) comes before
+// the own value and the other r-face neighbour (node i = N only) after it.
+template <int NQ, int V, typename T, typename Acc>
+__device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                                         const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha) {
+    constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
+    const unsigned e = unsigned(l0) / unsigned(NP);
+    const int q = l0 - int(e) * NP;
+    const int i0 = q % NQ, j = (q / NQ) % NQ, k = q / NQ2;
+    const unsigned t = e / unsigned(nx);
+    const int ex = int(e - t * unsigned(nx));
+    const unsigned tz = t / unsigned(ny);
+    const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
+    const int sy = j == 0 ? -1 : (j == N ? 1 : 0);
+    const int sz = k == 0 ? -1 : (k == N ? 1 : 0);
+    if ((sy < 0 && ey == 0) || (sy > 0 && ey == ny - 1) || (sz < 0 && ez == 0) || (sz > 0 && ez == nz - 1))
+        return Acc(0);                                    // on the cube boundary
+    const int oy = sy * (nx * NP - N * NQ);
+    const int oz = sz * (nx * ny * NP - N * NQ2);
+    const bool has_lo = i0 == 0 && ex > 0;                // node i = 0 has a lower r neighbour
+    const bool has_hi = i0 + V - 1 == N && ex < nx - 1;   // node i = N has a higher r neighbour
+    const bool mask_lo = i0 == 0 && ex == 0;
+    const bool mask_hi = i0 + V - 1 == N && ex == nx - 1;
+    const int z0 = sz < 0 ? oz : 0, z1 = sz > 0 ? oz : 0;
+    const int y0 = sy < 0 ? oy : 0, y1 = sy > 0 ? oy : 0;
+    T wv[4][V], lo[4], hi[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int cz = c >> 1, cy = c & 1;
+        const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
+        const int off = l0 + (cz ? z1 : z0) + (cy ? y1 : y0);
+        if (valid) {
+            vload_nc<T, V>(w + off, wv[c]);
+            lo[c] = has_lo ? __ldg(w + off - (NP - N)) : T(0);              // element ex-1, node i = N
+            hi[c] = has_hi ? __ldg(w + off + (V - 1) + (NP - N)) : T(0);   // element ex+1, node i = 0
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) wv[c][v] = T(0);
+            lo[c] = hi[c] = T(0);
+        }
+    }
+    T xv[V], pv[V], rv[V];
+    vload<T, V>(x + l0, xv);
+    vload<T, V>(p + l0, pv);
+    vload<T, V>(r + l0, rv);
+    Acc acc = Acc(0);
+    const bool owner_row = sy >= 0 && sz >= 0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const bool first_lo = (v == 0) && has_lo;
+        const bool last_hi = (v == V - 1) && has_hi;
+        Acc s = first_lo ? Acc(lo[0]) + Acc(wv[0][v]) : Acc(wv[0][v]);
+        if (last_hi) s = s + Acc(hi[0]);
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+            const int cz = c >> 1, cy = c & 1;
+            const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
+            if (!valid) continue;
+            if (first_lo) s = s + Acc(lo[c]);
+            s = s + Acc(wv[c][v]);
+            if (last_hi) s = s + Acc(hi[c]);
+        }
+        const bool masked = (v == 0 && mask_lo) || (v == V - 1 && mask_hi);
+        if (!masked) {
+            xv[v] = fma(alpha, pv[v], xv[v]);
+            rv[v] = fma(-alpha, T(s), rv[v]);
+            if (owner_row && !first_lo) acc = fma(Acc(rv[v]), Acc(rv[v]), acc);
+        }
+    }
+    vstore<T, V>(x + l0, xv);
+    vstore<T, V>(r + l0, rv);
+    return acc;
+}
+
 // One CG update step over all local nodes (grid-stride), with the <r, r>
 // reduction: per-thread partials in Acc, block and grid sums in FP64, and the
 // last block closes the iteration (beta, counter, stop flag).
@@ -111,8 +228,10 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
     if (st->done) return;
     const T alpha = T(st->alpha);
     Acc acc = Acc(0);
-    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nL; l += gridDim.x * blockDim.x)
-        acc += update_node<NQ, T, Acc>(x, r, p, w, l, nx, ny, nz, alpha);
+    constexpr int V = UpdVec<NQ, T>::value;
+    const int nv = nL / V;   // nL is a multiple of (N+1), hence of V
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nv; u += gridDim.x * blockDim.x)
+        acc += update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, nx, ny, nz, alpha);
     const double bs = block_sum(double(acc), red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
@@ -122,8 +241,9 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
 
 template <int NQ, typename T, typename Acc>
 static int launch_update_rows_nq(const Problem *P, T *x, T *r, const T *p, const T *w, CgState *st) {
-    int64_t blocks = (P->nL + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~54 nodes per thread at E = 32768, N = 7
+    constexpr int V = UpdVec<NQ, T>::value;
+    int64_t blocks = (P->nL / V + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~13-27 vectors per thread at E = 32768, N = 7
     cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(P->nL), P->nx,
                                                                                P->ny, P->nz, P->partials, st);
     count_launches(1);
