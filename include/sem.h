@@ -63,6 +63,8 @@ extern "C" {
                               /*        returns (sem_run then syncs its stream)   */
 #define SEM_ARG_OUT_INT    5  /* v.ptr : host int64_t*, as above                   */
 #define SEM_ARG_NONE       6  /* absent optional array                             */
+#define SEM_ARG_HOST       7  /* v.ptr : host array read or written during the     */
+                              /*        call only (small per-problem lists)       */
 
 typedef struct sem_arg {
     int32_t kind;
@@ -163,6 +165,23 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   "peak_fma"  dtype (0 f64, 1 f32), iters, OUT flops_per_s
  *               measured FMA issue rate of the FP64 or FP32 pipe (device fact
  *               for the ALU roofline; not part of the method)
+ *   "batch"     n, handles (HOST int64[n]), OUT batch
+ *               Group n problems (made with "mesh", any sizes and orders) for
+ *               batched solves.  Their local vectors are concatenated in the
+ *               given order (problem k at offset nL_0 + ... + nL_{k-1}).
+ *   "batch_info" batch, OUT n, OUT nL_total
+ *   "batch_solve" batch, b_all, x_all, tol, maxit, mode, inner_tol, max_outer,
+ *               OUT total_iters, OUT max_rel_res, [iters HOST int64[n]],
+ *               [rel_res HOST double[n]]
+ *               Solve every problem of the batch at once: each CG phase is one
+ *               persistent launch over all problems (dynamic work list, switch
+ *               on N), replayed from a CUDA graph.  mode 0: FP64 CG to tol;
+ *               mode 1 / 2: mixed-precision refinement (as "cg_mixed") with G
+ *               in BF16 / FP32.  A problem's iterates do not depend on the
+ *               other problems in the batch.  iters: CG iterations (mode 0) or
+ *               inner iterations (modes 1, 2); rel_res: recursive (mode 0) or
+ *               true (modes 1, 2) relative residual at exit.
+ *   "batch_free" batch
  * Unknown names return SEM_EKERNEL; wrong argument counts or kinds SEM_EARG. */
 int sem_run(const char *kernel, int nargs, const sem_arg *args);
 

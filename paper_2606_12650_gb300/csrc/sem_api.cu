@@ -4,6 +4,7 @@
 // pragmas lower to (init / update / run / sync / finalize, Sections IV-V).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -40,6 +41,7 @@ struct Context {
     std::map<void *, size_t> sizes;    // device pointer -> bytes
     std::map<uintptr_t, Mirror> mirrors;
     std::map<int64_t, Problem *> problems;
+    std::map<int64_t, Batch *> batches;
     int64_t next_handle = 1;
     int32_t *status_dev = nullptr;
     int32_t *status_pinned = nullptr;
@@ -213,6 +215,17 @@ struct ArgReader {
         }
         return dev;
     }
+    void *host(int k, size_t bytes, const char *name, bool optional = false) {
+        if (k >= nargs || args[k].kind == SEM_ARG_NONE) {
+            if (!optional) fail(SEM_EARG, std::string("host array ") + name + " missing");
+            return nullptr;
+        }
+        if (args[k].kind != SEM_ARG_HOST || (!args[k].v.ptr && bytes)) {
+            fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be SEM_ARG_HOST");
+            return nullptr;
+        }
+        return args[k].v.ptr;
+    }
     void *out(int k, int kind, const char *name) {
         if (k >= nargs || args[k].kind != kind || !args[k].v.ptr) {
             fail(SEM_EARG, std::string("argument ") + std::to_string(k) + " (" + name + ") must be an OUT pointer");
@@ -265,6 +278,7 @@ int run_mesh_free(ArgReader &R) {
     if (R.err) return R.err;
     auto it = g.problems.find(h);
     if (it == g.problems.end()) return R.fail(SEM_EHANDLE, "unknown problem handle");
+    if (!g.batches.empty()) return R.fail(SEM_EARG, "free the batches first (they hold their problems)");
     sync_stream("mesh_free");
     problem_destroy(it->second);
     g.problems.erase(it);
@@ -461,6 +475,103 @@ int run_cg_mixed(ArgReader &R) {
                        hist);
 }
 
+Batch *get_batch(ArgReader &R, int k) {
+    const int64_t h = R.i(k, "batch");
+    if (R.err) return nullptr;
+    auto it = g.batches.find(h);
+    if (it == g.batches.end()) {
+        R.fail(SEM_EHANDLE, "unknown batch handle " + std::to_string(h));
+        return nullptr;
+    }
+    return it->second;
+}
+
+int run_batch(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    const int64_t n = R.i(0, "n");
+    if (R.err) return R.err;
+    if (n < 1 || n > (1 << 20)) return R.fail(SEM_EARG, "n must be in [1, 2^20]");
+    const int64_t *hs = static_cast<const int64_t *>(R.host(1, size_t(n) * 8, "handles"));
+    int64_t *out = static_cast<int64_t *>(R.out(2, SEM_ARG_OUT_INT, "batch"));
+    if (R.err) return R.err;
+    std::vector<Problem *> ps;
+    for (int64_t k = 0; k < n; ++k) {
+        auto it = g.problems.find(hs[k]);
+        if (it == g.problems.end()) return R.fail(SEM_EHANDLE, "unknown problem handle " + std::to_string(hs[k]));
+        for (Problem *q : ps)
+            if (q == it->second) return R.fail(SEM_EARG, "a problem appears twice in the batch");
+        ps.push_back(it->second);
+    }
+    Batch *B = nullptr;
+    const int rc = batch_create(ps.data(), int(n), &B);
+    if (rc != SEM_OK) return rc;
+    const int64_t h = g.next_handle++;
+    g.batches[h] = B;
+    *out = h;
+    return SEM_OK;
+}
+
+int run_batch_info(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    Batch *B = get_batch(R, 0);
+    int64_t *o1 = static_cast<int64_t *>(R.out(1, SEM_ARG_OUT_INT, "n"));
+    int64_t *o2 = static_cast<int64_t *>(R.out(2, SEM_ARG_OUT_INT, "nL_total"));
+    if (R.err) return R.err;
+    *o1 = batch_size(B);
+    *o2 = batch_total_nodes(B);
+    return SEM_OK;
+}
+
+int run_batch_solve(ArgReader &R) {
+    if (!R.need(10)) return R.err;
+    Batch *B = get_batch(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(batch_total_nodes(B)) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b_all"));
+    double *x = static_cast<double *>(R.arr(2, vb, "x_all"));
+    const double tol = R.d(3, "tol");
+    const int64_t maxit = R.i(4, "maxit");
+    const int64_t mode = R.i(5, "mode");
+    const double inner_tol = R.d(6, "inner_tol");
+    const int64_t max_outer = R.i(7, "max_outer");
+    int64_t *o_it = static_cast<int64_t *>(R.out(8, SEM_ARG_OUT_INT, "total_iters"));
+    double *o_res = static_cast<double *>(R.out(9, SEM_ARG_OUT_DOUBLE, "max_rel_res"));
+    const int n = batch_size(B);
+    int64_t *its = static_cast<int64_t *>(R.host(10, size_t(n) * 8, "iters", true));
+    double *res = static_cast<double *>(R.host(11, size_t(n) * 8, "rel_res", true));
+    if (R.err) return R.err;
+    if (maxit < 1 || maxit > (1 << 30) || max_outer < 0 || max_outer > 1000)
+        return R.fail(SEM_EARG, "maxit must be in [1, 2^30] and max_outer in [0, 1000]");
+    if (b == x) return R.fail(SEM_EARG, "b_all and x_all must not alias");
+    std::vector<int64_t> it(n);
+    std::vector<double> rr(n);
+    const int rc = batch_solve(B, b, x, tol, int(maxit), int(mode), inner_tol, int(max_outer), it.data(), rr.data());
+    if (rc != SEM_OK) return rc;
+    int64_t tot = 0;
+    double mx = 0.0;
+    for (int k = 0; k < n; ++k) {
+        tot += it[k];
+        mx = std::max(mx, rr[k]);
+        if (its) its[k] = it[k];
+        if (res) res[k] = rr[k];
+    }
+    *o_it = tot;
+    *o_res = mx;
+    return SEM_OK;
+}
+
+int run_batch_free(ArgReader &R) {
+    if (!R.need(1)) return R.err;
+    const int64_t h = R.i(0, "batch");
+    if (R.err) return R.err;
+    auto it = g.batches.find(h);
+    if (it == g.batches.end()) return R.fail(SEM_EHANDLE, "unknown batch handle");
+    sync_stream("batch_free");
+    batch_destroy(it->second);
+    g.batches.erase(it);
+    return SEM_OK;
+}
+
 int run_cg_ax(ArgReader &R) {
     if (!R.need(1)) return R.err;
     Problem *P = get_problem(R, 0);
@@ -638,6 +749,10 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "ax32") rc = run_ax32(R);
     else if (k == "cg_ax32") rc = run_cg_ax32(R);
     else if (k == "cg_mixed") rc = run_cg_mixed(R);
+    else if (k == "batch") rc = run_batch(R);
+    else if (k == "batch_info") rc = run_batch_info(R);
+    else if (k == "batch_solve") rc = run_batch_solve(R);
+    else if (k == "batch_free") rc = run_batch_free(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
     else return set_error(SEM_EKERNEL, "sem_run: unknown kernel '" + k + "'");
     return rc;
@@ -653,6 +768,8 @@ int sem_sync(void) {
 int sem_finalize(void) {
     if (!g.up) return set_error(SEM_EINIT, "sem_finalize: not initialised");
     cudaStreamSynchronize(g.cur_stream);
+    for (auto &kv : g.batches) batch_destroy(kv.second);
+    g.batches.clear();
     for (auto &kv : g.problems) problem_destroy(kv.second);
     g.problems.clear();
     for (auto &kv : g.mirrors) dev_free(kv.second.dev);

@@ -86,46 +86,43 @@ struct AxShape {
     static constexpr size_t SMEM = 16 + 3 * size_t(SLAB) * sizeof(T);
 };
 
-template <int NQ, int EPB, typename T, typename GT, bool CG>
-__global__ void __launch_bounds__(AxShape<NQ, EPB, T>::NT)
-ax_kernel(const AxArgs<T, GT> P) {
+// One group of ne (<= EPB) elements starting at element e0, for a block of
+// AxShape<NQ, EPB, T>::NT threads.  regA: 16-byte aligned shared memory of
+// 3 * SLAB values; bar: an initialised mbarrier whose next completion is
+// phase `phase`; D: the NQ x NQ derivative matrix (anything indexable).
+// Returns false if the slab copy timed out (status set, copies drained).  In
+// CG mode, *part receives this thread's partial of <p, A_local p> (in T).
+template <int NQ, int EPB, typename T, typename GT, bool CG, typename DSrc>
+__device__ __forceinline__ bool ax_group(const T *x, T *y, T *p, const GT *G, const DSrc &D, T beta,
+                                         int64_t e0, int ne, T *regA, uint64_t *bar, uint32_t phase,
+                                         int32_t *status, T *part) {
     using S = AxShape<NQ, EPB, T>;
     constexpr int NQ2 = S::NQ2, NP = S::NP;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    T *regA = reinterpret_cast<T *>(smem + 16);
     T *regB = regA + S::SLAB;
     T *regC = regB + S::SLAB;
-
-    if (CG && P.st->done) return;  // solve finished: the rest of the graph is a no-op
-
     const int tid = threadIdx.x;
-    const int64_t e0 = int64_t(blockIdx.x) * EPB;
-    const int ne = int(min(int64_t(EPB), P.E - e0));
     const uint32_t bytes = uint32_t(ne) * NP * uint32_t(sizeof(T));
 
     // ---- stage the slab(s): TMA for the aligned middle, plain loads for the edges
-    const T *src1 = P.x + e0 * NP;                 // x (plain) or r (CG)
-    const T *src2 = CG ? P.p + e0 * NP : nullptr;  // p (CG)
+    const T *src1 = x + e0 * NP;                 // x (plain) or r (CG)
+    const T *src2 = CG ? p + e0 * NP : nullptr;  // p (CG)
     T *s1 = slab_dst(regA, src1);
     T *s2 = CG ? slab_dst(regB, src2) : nullptr;
     const SlabPlan pl1 = slab_plan(src1, bytes);
     SlabPlan pl2{0, 0, 0};
     if (CG) pl2 = slab_plan(src2, bytes);
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
     if (tid == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(bar, pl1.mid_bytes + pl2.mid_bytes);
         slab_issue(s1, src1, pl1, bar);
         if (CG) slab_issue(s2, src2, pl2, bar);
     }
     slab_edges(s1, src1, pl1, tid, S::NT);
     if (CG) slab_edges(s2, src2, pl2, tid, S::NT);
-    const bool ok = mbar_wait_bounded(bar, 0, P.status);
+    const bool ok = mbar_wait_bounded(bar, phase, status);
     if (__syncthreads_or(!ok)) {
-        mbar_wait_bounded(bar, 0, nullptr);  // let copies in flight land before exit
-        return;
+        mbar_wait_bounded(bar, phase, nullptr);  // let copies in flight land before leaving
+        return false;
     }
 
     const int eb = tid / NQ2;
@@ -136,7 +133,6 @@ ax_kernel(const AxArgs<T, GT> P) {
 
     T xk[NQ];
     if (CG) {
-        const T beta = T(P.st->beta);
         if (act) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
@@ -144,7 +140,7 @@ ax_kernel(const AxArgs<T, GT> P) {
                 const T pn = fma(beta, s2[q], s1[q]);
                 s2[q] = pn;
                 xk[k] = pn;
-                P.p[nb + k * NQ2 + ij] = pn;
+                p[nb + k * NQ2 + ij] = pn;
             }
         }
         __syncthreads();
@@ -159,10 +155,10 @@ ax_kernel(const AxArgs<T, GT> P) {
     T Di[NQ], Dj[NQ], Dti[NQ], Dtj[NQ];
 #pragma unroll
     for (int l = 0; l < NQ; ++l) {
-        Di[l] = P.D[i * NQ + l];
-        Dj[l] = P.D[j * NQ + l];
-        Dti[l] = P.D[l * NQ + i];
-        Dtj[l] = P.D[l * NQ + j];
+        Di[l] = D[i * NQ + l];
+        Dj[l] = D[j * NQ + l];
+        Dti[l] = D[l * NQ + i];
+        Dtj[l] = D[l * NQ + j];
     }
 
     // ---- gradient in reference coordinates, then the geometric factors
@@ -175,10 +171,10 @@ ax_kernel(const AxArgs<T, GT> P) {
             for (int l = 0; l < NQ; ++l) {
                 ur = fma(Di[l], sx[k * NQ2 + j * NQ + l], ur);
                 us = fma(Dj[l], sx[k * NQ2 + l * NQ + i], us);
-                ut = fma(P.D[k * NQ + l], xk[l], ut);
+                ut = fma(D[k * NQ + l], xk[l], ut);
             }
             T g[6];  // (rr, rs, rt, ss, st, tt)
-            load_g6(P.G, nb + k * NQ2 + ij, g);
+            load_g6(G, nb + k * NQ2 + ij, g);
             s_wr[k * NQ2 + ij] = g[0] * ur + g[1] * us + g[2] * ut;
             s_ws[k * NQ2 + ij] = g[1] * ur + g[3] * us + g[4] * ut;
             wt[k] = g[2] * ur + g[4] * us + g[5] * ut;
@@ -197,17 +193,47 @@ ax_kernel(const AxArgs<T, GT> P) {
 #pragma unroll
             for (int l = 0; l < NQ; ++l) yv = fma(Dtj[l], s_ws[k * NQ2 + l * NQ + i], yv);
 #pragma unroll
-            for (int l = 0; l < NQ; ++l) yv = fma(P.D[l * NQ + k], wt[l], yv);
-            P.y[nb + k * NQ2 + ij] = yv;
+            for (int l = 0; l < NQ; ++l) yv = fma(D[l * NQ + k], wt[l], yv);
+            y[nb + k * NQ2 + ij] = yv;
             if (CG) acc = fma(xk[k], yv, acc);
         }
     }
+    if (CG) *part = acc;
+    return true;
+}
+
+// Indexes the derivative matrix held in the kernel parameters.
+template <typename T, typename GT>
+struct ParamD {
+    const AxArgs<T, GT> &a;
+    __device__ __forceinline__ T operator[](int q) const { return a.D[q]; }
+};
+
+template <int NQ, int EPB, typename T, typename GT, bool CG>
+__global__ void __launch_bounds__(AxShape<NQ, EPB, T>::NT)
+ax_kernel(const AxArgs<T, GT> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *regA = reinterpret_cast<T *>(smem + 16);
+
+    if (CG && P.st->done) return;  // solve finished: the rest of the graph is a no-op
+
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    const int64_t e0 = int64_t(blockIdx.x) * EPB;
+    const int ne = int(min(int64_t(EPB), P.E - e0));
+    const T beta = CG ? T(P.st->beta) : T(0);
+    T part = T(0);
+    const ParamD<T, GT> D{P};
+    if (!ax_group<NQ, EPB, T, GT, CG>(P.x, P.y, P.p, P.G, D, beta, e0, ne, regA, bar, 0u, P.status, &part))
+        return;
     if (CG) {
         // the column's partial is formed in T; the block and grid sums are FP64
-        const double bs = block_sum(double(acc), red);
+        const double bs = block_sum(double(part), red);
         if (publish_partial(bs, P.partials, &P.st->ticket_ax)) {
             const double pap = finish_partials(P.partials, int(gridDim.x), &P.st->ticket_ax, red);
-            if (tid == 0) {
+            if (threadIdx.x == 0) {
                 P.st->pap = pap;
                 P.st->alpha = P.st->rho / pap;
             }

@@ -106,6 +106,7 @@ int set_error(int code, const std::string &msg);
 int cuda_check(cudaError_t err, const char *what);
 
 // ---- setup (sem_setup.cu) --------------------------------------------------
+void gll_rule_and_derivative(int N, double *xi, double *w, double *D);   // D row-major (N+1)^2
 int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out);
 void problem_destroy(Problem *P);
 int launch_nodes(const Problem *P, const double *verts_dev, double *X);
@@ -133,6 +134,15 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
 int launch_cg_update(const Problem *P);
 int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, double *hist,
              int64_t *iters, double *rel_res);
+
+// ---- batches (sem_batch.cu) -------------------------------------------------
+struct Batch;
+int batch_create(Problem **probs, int n, Batch **out);
+void batch_destroy(Batch *B);
+int64_t batch_total_nodes(const Batch *B);
+int batch_size(const Batch *B);
+int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int maxit, int mode, double inner_tol,
+                int max_outer, int64_t *iters, double *res);
 
 // ---- device facts (sem_probe.cu) --------------------------------------------
 int probe_fma_rate(int dtype, int iters, double *flops_per_s);   // dtype 0: f64, 1: f32

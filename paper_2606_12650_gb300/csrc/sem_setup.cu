@@ -97,6 +97,11 @@ static void barycentric_derivative(int N, const double *xi, double *D) {
     }
 }
 
+void gll_rule_and_derivative(int N, double *xi, double *w, double *D) {
+    gll_rule(N, xi, w);
+    barycentric_derivative(N, xi, D);
+}
+
 // ---------------------------------------------------------------- geometry
 struct GeomArgs {
     const double *verts;

@@ -92,3 +92,33 @@ class Mesh:
         if self.handle:
             sem.run("mesh_free", self.handle)
             self.handle = 0
+
+
+class Batch:
+    """Problems solved together: every CG phase is one persistent launch."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        hs = np.array([m.handle for m in self.meshes], dtype=np.int64)
+        h = sem.OutInt()
+        sem.run("batch", len(hs), sem.HostArray(hs), h)
+        self.handle = h.value
+        n, tot = sem.OutInt(), sem.OutInt()
+        sem.run("batch_info", self.handle, n, tot)
+        self.n, self.nL_total = n.value, tot.value
+        self.offsets = np.concatenate([[0], np.cumsum([m.nL for m in self.meshes])])[:-1]
+
+    def solve(self, b_all, x_all, tol: float, maxit: int = 100000, mode: int = 0,
+              inner_tol: float = 1e-3, max_outer: int = 50):
+        """Returns (iters per problem, relative residual per problem)."""
+        its = np.zeros(self.n, dtype=np.int64)
+        res = np.zeros(self.n, dtype=np.float64)
+        tot, mx = sem.OutInt(), sem.OutDouble()
+        sem.run("batch_solve", self.handle, b_all, x_all, float(tol), int(maxit), int(mode),
+                float(inner_tol), int(max_outer), tot, mx, sem.HostArray(its), sem.HostArray(res))
+        return its, res
+
+    def free(self):
+        if self.handle:
+            sem.run("batch_free", self.handle)
+            self.handle = 0

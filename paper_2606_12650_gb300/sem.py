@@ -40,7 +40,7 @@ SEM_EHANDLE = -10
 
 SEM_ALLOC, SEM_TO, SEM_FROM, SEM_FREE = 0, 1, 2, 3
 
-ARG_INT, ARG_DOUBLE, ARG_MAPPED, ARG_DEVICE, ARG_OUT_DOUBLE, ARG_OUT_INT, ARG_NONE = range(7)
+ARG_INT, ARG_DOUBLE, ARG_MAPPED, ARG_DEVICE, ARG_OUT_DOUBLE, ARG_OUT_INT, ARG_NONE, ARG_HOST = range(8)
 
 EXPORTS = ("sem_init", "sem_update", "sem_run", "sem_sync", "sem_finalize", "sem_last_error",
            "sem_set_allocator", "sem_set_stream", "sem_launch_count", "sem_dot_noalloc")
@@ -143,6 +143,16 @@ class DevicePtr(int):
     """A raw device address (SEM_ARG_DEVICE)."""
 
 
+class HostArray:
+    """A small host numpy array passed by address for the duration of the
+    call (SEM_ARG_HOST): read and/or written by libsem."""
+
+    def __init__(self, arr):
+        if not arr.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        self.arr = arr
+
+
 def _is_torch_tensor(a) -> bool:
     t = type(a)
     return t.__module__.startswith("torch") and t.__name__ in ("Tensor", "Parameter")
@@ -158,6 +168,9 @@ def _marshal(a) -> SemArg:
     elif isinstance(a, OutDouble):
         arg.kind = ARG_OUT_DOUBLE
         arg.v.ptr = ctypes.cast(ctypes.pointer(a._c), ctypes.c_void_p).value
+    elif isinstance(a, HostArray):
+        arg.kind = ARG_HOST
+        arg.v.ptr = a.arr.__array_interface__["data"][0]
     elif isinstance(a, DevicePtr):
         arg.kind = ARG_DEVICE
         arg.v.ptr = int(a)
