@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
         else { xin = reinterpret_cast<const T *>(P.r32); yout = reinterpret_cast<T *>(P.w32); pv = reinterpret_cast<T *>(P.p32); }
         const GT *G = prob_G<GT>(P);
         T pt = T(0);
-        bool ok = true;
+        bool ok = true, used = true;
         switch (item.nq) {
 #define SEM_BAX(Q)                                                                                     \
     case Q:                                                                                            \
@@ -227,9 +227,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
         break;
             SEM_BAX(2) SEM_BAX(3) SEM_BAX(4) SEM_BAX(5) SEM_BAX(6) SEM_BAX(7) SEM_BAX(8) SEM_BAX(9) SEM_BAX(10)
 #undef SEM_BAX
-            default: break;
+            default: used = false; break;
         }
-        phase ^= 1u;
+        if (used) phase ^= 1u;
         if (!ok) return;  // timed out: the status word reports it; the solve is abandoned
         if (CG) {
             const double bs = block_sum(double(pt), red);
