@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=1e-3, help="inner FP32 CG residual reduction")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -284,6 +286,11 @@ def run_ours(a):
     if not a.no_mixed:
         mixed = run_mixed(a, M, b, x, t_max, world, barrier, stream, sem, torch, dist)
 
+    # ---- batched: many uneven problems, one persistent launch per CG phase
+    batched = None
+    if not a.no_batched:
+        batched = run_batched(a, world, rank, barrier, stream, sem, torch, dist)
+
     # ---- end to end through the public API, host buffers
     e2e = None
     if not a.no_e2e:
@@ -335,7 +342,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "mixed": mixed,
+                "mixed": mixed, "batched": batched,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
@@ -422,6 +429,62 @@ def run_mixed(a, M, b, x64, t64_ms, world, barrier, stream, sem, torch, dist):
             "tol_1e-10": {"fp64_cg_iters": it10, "fp64_ms": 1e3 * t_fp64_10,
                           "mixed_inner_iters": in10, "mixed_outer_iters": out10, "mixed_ms": 1e3 * t_mix_10,
                           "mixed_rel_res_true": res10, "err_vs_fp64_cg_inf": err10}}
+
+
+def run_batched(a, world, rank, barrier, stream, sem, torch, dist):
+    """256 independent problems (E log-uniform in [8, 4096] as near-cubic boxes,
+    N uniform in {3, 5, 7, 9}, jitter 5 %, random right-hand sides), each CG
+    phase of all of them one persistent launch: FP64 CG and mixed refinement
+    to 1e-8.  Throughput counts every problem's own iterations."""
+    import numpy as np
+    from paper_2606_12650_gb300 import Batch, Mesh
+    from paper_2606_12650_gb300.inputs import batch_specs, box_vertices, normal_field
+    specs = batch_specs(a.batch_count, seed=4 + 1000 * rank, e_lo=8, e_hi=4096, orders=(3, 5, 7, 9))
+    t0 = time.perf_counter()
+    meshes, bs = [], []
+    for s in specs:
+        jit = 0.05 if min(s["nx"], s["ny"], s["nz"]) > 1 else 0.0
+        m = Mesh(s["nx"], s["ny"], s["nz"], s["N"], box_vertices(s["nx"], s["ny"], s["nz"], jit, seed=s["mesh_seed"]))
+        f = torch.from_numpy(normal_field(m.nL, s["rhs_seed"])).cuda()
+        m.gs(f)
+        m.mask(f)
+        meshes.append(m)
+        bs.append(f)
+    B = Batch(meshes)
+    b_all = torch.cat(bs)
+    del bs
+    x_all = torch.empty_like(b_all)
+    setup_s = time.perf_counter() - t0
+    gdof_per_iter = np.array([m.E * m.N ** 3 for m in meshes], dtype=np.float64)
+    out = {"workload": f"{len(meshes)} problems, E log-uniform [8, 4096] (near-cubic boxes), N in {{3,5,7,9}}, "
+                       f"jitter 5%, random RHS; tol {a.tol:g}; every CG phase one persistent launch",
+           "problems": len(meshes), "local_dofs_total": int(B.nL_total),
+           "E_total": int(sum(m.E for m in meshes)), "setup_s": setup_s}
+    for mode, name in ((0, "fp64"), (1, "mixed_bf16")):
+        B.solve(b_all, x_all, a.tol, a.maxit, mode, a.inner_tol)    # warm-up (graph capture)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, res = B.solve(b_all, x_all, a.tol, a.maxit, mode, a.inner_tol)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        dofs = float((gdof_per_iter * its).sum())
+        if world > 1:
+            tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms = float(tt.item())
+            dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
+            dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+            dofs = float(dd.item())
+        out[name] = {"ms": ms, "gdofs": dofs / (ms * 1e-3) / 1e9, "solves_per_s": 1e3 * len(meshes) * world / ms,
+                     "iters_total": int(its.sum()), "iters_max": int(its.max()), "max_rel_res": float(res.max())}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed_bf16"]["ms"]
+    B.free()
+    for m in meshes:
+        m.free()
+    return out
 
 
 def main():
