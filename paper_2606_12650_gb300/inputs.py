@@ -16,7 +16,9 @@ The recipes below stand in for it:
 * ``normal_field`` -- i.i.d. standard normal values (random right-hand sides,
   random operands for operator parity).
 * ``near_cubic`` -- factor an element count into nx*ny*nz as close to a cube
-  as possible (the paper's E = 2^k sweep).
+  as possible (the paper's E = 2^k sweep, where exact factors are cubic).
+* ``cubic_box`` -- sides of a box of about E elements, all within one of
+  E^(1/3) (problem mixes; the actual E is recorded).
 * ``batch_specs`` / ``arrival_times`` -- problem mixes for batched and served
   runs (element counts log-uniform, orders from a set, Poisson arrivals).
 """
@@ -30,6 +32,7 @@ __all__ = [
     "box_vertices",
     "normal_field",
     "near_cubic",
+    "cubic_box",
     "batch_specs",
     "arrival_times",
 ]
@@ -95,18 +98,28 @@ def near_cubic(E: int) -> tuple[int, int, int]:
     return best  # (largest, middle, smallest)
 
 
+def cubic_box(E: float) -> tuple[int, int, int]:
+    """Sides of a box of about E elements with all sides within one of
+    E^(1/3) (elements of aspect ratio ~1); the product is the actual E."""
+    nx = max(1, int(round(E ** (1.0 / 3.0))))
+    ny = max(1, int(round(math.sqrt(E / nx))))
+    nz = max(1, int(round(E / (nx * ny))))
+    return nx, ny, nz
+
+
 def batch_specs(count: int, seed: int, e_lo: int = 8, e_hi: int = 4096,
                 orders=(3, 5, 7, 9)) -> list[dict]:
-    """Problem mix: E = round(exp(U[ln e_lo, ln e_hi])) realised as a near-cubic
-    box, N drawn uniformly from ``orders``; each problem also gets its own
-    jitter seed and right-hand-side seed."""
+    """Problem mix: a target E = exp(U[ln e_lo, ln e_hi]) realised as a
+    near-cubic box (``cubic_box``; the actual E = nx ny nz is in the spec), N
+    drawn uniformly from ``orders``; each problem also gets its own jitter seed
+    and right-hand-side seed."""
     rng = np.random.default_rng(seed)
     out = []
     for q in range(count):
-        E = int(round(math.exp(rng.uniform(math.log(e_lo), math.log(e_hi)))))
+        target = math.exp(rng.uniform(math.log(e_lo), math.log(e_hi)))
         N = int(orders[rng.integers(len(orders))])
-        nx, ny, nz = near_cubic(E)
-        out.append({"nx": nx, "ny": ny, "nz": nz, "N": N,
+        nx, ny, nz = cubic_box(target)
+        out.append({"nx": nx, "ny": ny, "nz": nz, "N": N, "E": nx * ny * nz,
                     "mesh_seed": int(rng.integers(1 << 31)),
                     "rhs_seed": int(rng.integers(1 << 31))})
     return out

@@ -317,3 +317,15 @@ def test_cg_fixed_iterations_history(oracle_mod):
     # the recursive residual tracks the true one in the early iterations
     r = b - P.apply(sol)
     assert abs(math.sqrt(P.dot(r, r)) - hist[-1]) < 1e-8 * hist[0]
+
+
+def test_input_mixes_are_near_cubic():
+    """Problem mixes realise a log-uniform element count as boxes of aspect
+    ratio ~1 (a prime count must not become an E x 1 x 1 box)."""
+    from paper_2606_12650_gb300.inputs import batch_specs, cubic_box
+    for s in batch_specs(256, seed=4):
+        sides = (s["nx"], s["ny"], s["nz"])
+        assert s["E"] == s["nx"] * s["ny"] * s["nz"]
+        assert max(sides) - min(sides) <= 2
+        assert 8 / 2 <= s["E"] <= 4096 * 1.5
+    assert cubic_box(4093) == (16, 16, 16) and cubic_box(8) == (2, 2, 2)
