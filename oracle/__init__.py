@@ -78,6 +78,12 @@ def _load():
                                ctypes.c_long, _u8, _d, _d, _d, ctypes.c_int,
                                ctypes.c_double, _d]
         lib.orc_cg.restype = ctypes.c_int
+        lib.orc_diag.argtypes = [ctypes.c_long, ctypes.c_int, _d, _d, ctypes.c_long, _i64, ctypes.c_long,
+                                 _u8, _d]
+        lib.orc_diag.restype = None
+        lib.orc_pcg.argtypes = [ctypes.c_long, ctypes.c_int, _d, _d, ctypes.c_long, _i64,
+                                ctypes.c_long, _u8, _d, _d, _d, _d, ctypes.c_int, ctypes.c_double, _d]
+        lib.orc_pcg.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -230,6 +236,29 @@ class Problem:
         it = lib.orc_cg(self.E, self.N, _p(self.D), _p(self.G), self.nL,
                         _p(self.gid, _i64), self.nG, _p(self.onbdry, _u8), _p(self.c),
                         _p(b), _p(x), int(maxit), float(tol), _p(hist))
+        return x, it, hist[: it + 1].copy()
+
+    def diag(self):
+        """Diagonal of the assembled, masked operator (zero on masked nodes)."""
+        lib = _load()
+        d = np.empty(self.nL)
+        lib.orc_diag(self.E, self.N, _p(self.D), _p(self.G), self.nL, _p(self.gid, _i64), self.nG,
+                     _p(self.onbdry, _u8), _p(d))
+        return d
+
+    def pcg(self, b, maxit=100, tol=0.0, dinv=None):
+        """Jacobi-preconditioned CG from x0 = 0; hist[k] = ||r_k||_c.
+        Returns (x, iters, hist)."""
+        lib = _load()
+        if dinv is None:
+            d = self.diag()
+            dinv = np.where(d > 0.0, 1.0 / np.where(d > 0.0, d, 1.0), 0.0)
+        b = _f64(b)
+        x = np.empty_like(b)
+        hist = np.zeros(maxit + 1)
+        it = lib.orc_pcg(self.E, self.N, _p(self.D), _p(self.G), self.nL, _p(self.gid, _i64), self.nG,
+                         _p(self.onbdry, _u8), _p(self.c), _p(_f64(dinv)), _p(b), _p(x), int(maxit),
+                         float(tol), _p(hist))
         return x, it, hist[: it + 1].copy()
 
     def true_residual(self, b, x):

@@ -402,3 +402,83 @@ int orc_cg(long E, int N, const double *D, const double *G, long nL,
     free(r); free(p); free(w); free(sum); free(seen);
     return it;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Diagonal of the assembled, masked operator, from its definition: for    */
+/* every local node q of every element, (A_e e_q)_q with e_q the unit vector */
+/* at q (one local operator application per node -- slow, plain), then the */
+/* direct-stiffness sum and the mask.  d: nL entries.  (Jacobi              */
+/* preconditioning is the original Nekbone method, Section VIII-A.)          */
+/* ------------------------------------------------------------------------ */
+void orc_diag(long E, int N, const double *D, const double *G, long nL, const int64_t *gid, long nG,
+              const uint8_t *onbdry, double *d)
+{
+    int n = N + 1;
+    int np = n * n * n;
+    double *u = (double *)calloc((size_t)np, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * np);
+    for (long e = 0; e < E; ++e) {
+        for (int q = 0; q < np; ++q) {
+            u[q] = 1.0;
+            orc_ax_local(1, N, D, G + 6L * np * e, u, y);
+            d[(long)np * e + q] = y[q];
+            u[q] = 0.0;
+        }
+    }
+    free(u); free(y);
+    double *sum = (double *)malloc(sizeof(double) * nG);
+    uint8_t *seen = (uint8_t *)malloc((size_t)nG);
+    orc_gs(nL, gid, nG, d, sum, seen);
+    orc_mask(nL, onbdry, d);
+    free(sum); free(seen);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Jacobi-preconditioned CG (textbook):  z = M^-1 r with M = diag(A)         */
+/* (zero on masked nodes), x = 0, r = b, z = M^-1 r, rho = <r,z>, p = z;    */
+/* repeat: w = A p; alpha = rho/<p,w>; x += alpha p; r -= alpha w;           */
+/*         z = M^-1 r; rho' = <r,z>; stop if ||r||_c/||b||_c <= tol or       */
+/*         maxit; beta = rho'/rho; p = z + beta p.                           */
+/* hist[k] = ||r_k||_c.  Returns the number of iterations.                   */
+/* ------------------------------------------------------------------------ */
+int orc_pcg(long E, int N, const double *D, const double *G, long nL,
+            const int64_t *gid, long nG, const uint8_t *onbdry, const double *c,
+            const double *dinv, const double *b, double *x, int maxit, double tol, double *hist)
+{
+    double *r = (double *)malloc(sizeof(double) * nL);
+    double *z = (double *)malloc(sizeof(double) * nL);
+    double *p = (double *)malloc(sizeof(double) * nL);
+    double *w = (double *)malloc(sizeof(double) * nL);
+    double *sum = (double *)malloc(sizeof(double) * nG);
+    uint8_t *seen = (uint8_t *)malloc((size_t)nG);
+    for (long l = 0; l < nL; ++l) {
+        x[l] = 0.0;
+        r[l] = b[l];
+        z[l] = dinv[l] * r[l];
+        p[l] = z[l];
+    }
+    double bb = orc_dot(nL, c, b, b);
+    double rho = orc_dot(nL, c, r, z);
+    if (hist) hist[0] = sqrt(bb);
+    int it = 0;
+    if (bb > 0.0) {
+        while (it < maxit) {
+            orc_apply(E, N, D, G, nL, gid, nG, onbdry, p, w, sum, seen);
+            double pw = orc_dot(nL, c, p, w);
+            double alpha = rho / pw;
+            for (long l = 0; l < nL; ++l) x[l] += alpha * p[l];
+            for (long l = 0; l < nL; ++l) r[l] -= alpha * w[l];
+            for (long l = 0; l < nL; ++l) z[l] = dinv[l] * r[l];
+            double rho_new = orc_dot(nL, c, r, z);
+            double rr = orc_dot(nL, c, r, r);
+            ++it;
+            if (hist) hist[it] = sqrt(rr);
+            if (tol > 0.0 && sqrt(rr / bb) <= tol) break;
+            double beta = rho_new / rho;
+            rho = rho_new;
+            for (long l = 0; l < nL; ++l) p[l] = z[l] + beta * p[l];
+        }
+    }
+    free(r); free(z); free(p); free(w); free(sum); free(seen);
+    return it;
+}

@@ -28,6 +28,9 @@ MUTATIONS = {
     "gs_last_copy_wins": ("else sum[g] += u[l];", "else sum[g] = u[l];"),
     "mask_misses_a_face": ("gz == 0 || gz == mz", "gz == 0"),
     "geometry_weight_missing": ("double W = w[i] * w[j] * w[k];", "double W = w[i] * w[j];"),
+    "pcg_unpreconditioned_z": ("for (long l = 0; l < nL; ++l) z[l] = dinv[l] * r[l];",
+                               "for (long l = 0; l < nL; ++l) z[l] = r[l];"),
+    "diag_wrong_entry": ("d[(long)np * e + q] = y[q];", "d[(long)np * e + q] = y[0];"),
     "ut_wrong_stride": ("ut += D[k * n + m] * ue[i + n * (j + n * m)];",
                         "ut += D[k * n + m] * ue[i + n * (m + n * j)];"),
 }

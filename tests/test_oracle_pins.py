@@ -329,3 +329,54 @@ def test_input_mixes_are_near_cubic():
         assert max(sides) - min(sides) <= 2
         assert 8 / 2 <= s["E"] <= 4096 * 1.5
     assert cubic_box(4093) == (16, 16, 16) and cubic_box(8) == (2, 2, 2)
+
+
+# --------------------------------------------------------------------------- Jacobi
+@pytest.mark.parametrize("dims,N,seed", [((2, 2, 2), 2, 5), ((2, 1, 2), 3, 3)])
+def test_diag_is_the_dense_weak_form_diagonal(oracle_mod, dims, N, seed):
+    nx, ny, nz = dims
+    verts = box_vertices(nx, ny, nz, 0.05, seed=seed) if min(dims) > 1 else \
+        box_vertices(nx, ny, nz, 0.0) + 0.1 * box_vertices(nx, ny, nz, 0.0)[:, [1, 2, 0]] ** 2
+    P = oracle_mod.Problem(nx, ny, nz, N, verts)
+    A_ref, ids = dense_stiffness(nx, ny, nz, N, verts, P.xi, P.w)
+    d = P.diag()
+    ref = np.diag(A_ref)[ids] * (P.onbdry == 0)
+    np.testing.assert_allclose(d, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_diag_matches_closed_form(oracle_mod):
+    """Local diagonal of y = D_a^T G_ab D_b u at node (i,j,k):
+    sum_a D_ai^2 G_rr(a,j,k) + sum_b D_bj^2 G_ss(i,b,k) + sum_c D_ck^2 G_tt(i,j,c)
+    + 2 (D_ii D_jj G_rs + D_ii D_kk G_rt + D_jj D_kk G_st)(i,j,k)."""
+    N, nx, ny, nz = 4, 2, 3, 2
+    P = oracle_mod.Problem(nx, ny, nz, N, box_vertices(nx, ny, nz, 0.05, seed=9))
+    n = N + 1
+    G = P.G.reshape(P.E, n, n, n, 6)    # [e][k][j][i][m]
+    D = P.D
+    loc = np.zeros((P.E, n, n, n))
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                v = sum(D[a, i] ** 2 * G[:, k, j, a, 0] for a in range(n))
+                v = v + sum(D[b, j] ** 2 * G[:, k, b, i, 3] for b in range(n))
+                v = v + sum(D[c, k] ** 2 * G[:, c, j, i, 5] for c in range(n))
+                v = v + 2 * (D[i, i] * D[j, j] * G[:, k, j, i, 1] + D[i, i] * D[k, k] * G[:, k, j, i, 2]
+                             + D[j, j] * D[k, k] * G[:, k, j, i, 4])
+                loc[:, k, j, i] = v
+    ref = P.mask(P.gs(loc.ravel()))
+    np.testing.assert_allclose(P.diag(), ref, rtol=1e-13, atol=1e-15)
+
+
+def test_pcg_reaches_dense_solution_in_fewer_iterations(oracle_mod):
+    P = oracle_mod.Problem(3, 3, 3, 5, box_vertices(3, 3, 3, 0.05, seed=4))
+    b = P.rhs_random(7)
+    x_cg, it_cg, _ = P.cg(b, maxit=20000, tol=1e-10)
+    x_pcg, it_pcg, hist = P.pcg(b, maxit=20000, tol=1e-10)
+    assert P.true_residual(b, x_pcg) < 2e-10
+    assert np.abs(x_pcg - x_cg).max() < 1e-7 * np.abs(x_cg).max()
+    assert it_pcg < it_cg
+    assert abs(hist[0] - np.sqrt(P.dot(b, b))) < 1e-14 * hist[0]
+    # with M = I (dinv = 1 on unmasked nodes) PCG is CG
+    one = (P.onbdry == 0).astype(float)
+    x1, it1, _ = P.pcg(b, maxit=20000, tol=1e-10, dinv=one)
+    assert it1 == it_cg and np.abs(x1 - x_cg).max() <= 1e-12 * np.abs(x_cg).max()
