@@ -24,7 +24,8 @@ MUTATIONS = {
     "gll_weight_formula": ("w[j] = 2.0 / (N * (N + 1.0) * P * P);",
                            "w[j] = 2.0 / ((N + 1.0) * (N + 1.0) * P * P);"),
     "D_corner_entry": ("v = N * (N + 1.0) / 4.0;", "v = N * (N + 1.0) / 2.0;"),
-    "cg_beta_inverted": ("double beta = rho_new / rho;", "double beta = rho / rho_new;"),
+    "cg_beta_inverted": ("for (long l = 0; l < nL; ++l) p[l] = r[l] + beta * p[l];",
+                         "for (long l = 0; l < nL; ++l) p[l] = r[l] + (1.0 / beta) * p[l];"),
     "gs_last_copy_wins": ("else sum[g] += u[l];", "else sum[g] = u[l];"),
     "mask_misses_a_face": ("gz == 0 || gz == mz", "gz == 0"),
     "geometry_weight_missing": ("double W = w[i] * w[j] * w[k];", "double W = w[i] * w[j];"),
