@@ -140,6 +140,12 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               maxit).  rho = <r,r>_c.  hist (maxit+1 doubles, optional)
  *               receives sqrt(rho_k).  rel_res = sqrt(rho/rho_0) at exit.
  *   "true_res"  handle, b, x, OUT d     ||b - A x||_c / ||b||_c (FP64)
+ *   "pcg_solve" handle, b, x, tol, maxit, OUT iters, OUT rel_res, [hist]
+ *               Jacobi-preconditioned CG (the original Nekbone method,
+ *               Section VIII-A): M = diag of the assembled, masked operator;
+ *               stops when ||r||_c/||b||_c <= tol; hist[k] = ||r_k||_c.
+ *   "jacobi"    handle, dinv[nL]        the preconditioner 1/diag(A) (0 on
+ *                                       masked nodes), FP64
  *   "ax32"      handle, x, y, gprec     y = A_local x in FP32 (x, y: nL floats);
  *                                       geometric factors rounded to nearest
  *                                       even from FP64 to FP32 (gprec 0) or

@@ -590,6 +590,37 @@ int run_peak_fma(ArgReader &R) {
     return probe_fma_rate(int(dtype), int(iters), out);
 }
 
+int run_pcg_solve(ArgReader &R) {
+    if (!R.need(7)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b"));
+    double *x = static_cast<double *>(R.arr(2, vb, "x"));
+    const double tol = R.d(3, "tol");
+    const int64_t maxit = R.i(4, "maxit");
+    int64_t *oit = static_cast<int64_t *>(R.out(5, SEM_ARG_OUT_INT, "iters"));
+    double *ores = static_cast<double *>(R.out(6, SEM_ARG_OUT_DOUBLE, "rel_res"));
+    if (R.err) return R.err;
+    if (maxit < 0 || maxit > (1 << 30)) return R.fail(SEM_EARG, "maxit must be in [0, 2^30]");
+    double *hist = static_cast<double *>(R.arr(7, size_t(maxit + 1) * sizeof(double), "hist", true));
+    if (R.err) return R.err;
+    if (b == x) return R.fail(SEM_EARG, "b and x must not alias");
+    return pcg_solve(P, b, x, tol, int(maxit), hist, oit, ores);
+}
+
+int run_jacobi(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    Problem *P = get_problem(R, 0);
+    if (R.err) return R.err;
+    double *out = static_cast<double *>(R.arr(1, size_t(P->nL) * sizeof(double), "dinv"));
+    if (R.err) return R.err;
+    const int rc = jacobi_prepare(P);
+    if (rc != SEM_OK) return rc;
+    return cuda_check(cudaMemcpyAsync(out, P->dinv, size_t(P->nL) * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      g.cur_stream), "jacobi: copy");
+}
+
 int run_true_res(ArgReader &R) {
     if (!R.need(4)) return R.err;
     Problem *P = get_problem(R, 0);
@@ -745,6 +776,8 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "rhs_sin") rc = run_rhs(R, true);
     else if (k == "cg_solve") rc = run_cg_solve(R);
     else if (k == "true_res") rc = run_true_res(R);
+    else if (k == "pcg_solve") rc = run_pcg_solve(R);
+    else if (k == "jacobi") rc = run_jacobi(R);
     else if (k == "cg_ax") rc = run_cg_ax(R);
     else if (k == "ax32") rc = run_ax32(R);
     else if (k == "cg_ax32") rc = run_cg_ax32(R);

@@ -22,4 +22,13 @@ int launch_ax_cg(const Problem *Pb) {
     return launch_ax_any<double, double, true>(Pb, a);
 }
 
+int launch_ax_pcg(const Problem *Pb) {
+    AxArgs<double, double> a = ax_args<double, double>(Pb, Pb->G, Pb->partials, Pb->st);
+    a.x = Pb->r;
+    a.y = Pb->w;
+    a.p = Pb->p;
+    a.dinv = Pb->dinv;
+    return launch_ax_any<double, double, true, true>(Pb, a);
+}
+
 }  // namespace sem

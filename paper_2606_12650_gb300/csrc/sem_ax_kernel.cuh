@@ -47,6 +47,7 @@ struct AxArgs {
     double *partials;
     CgState *st;
     int32_t *status;
+    const T *dinv;      // PCG: Jacobi inverse diagonal
     int64_t E;
     T D[kMaxQ * kMaxQ];
 };
@@ -92,10 +93,10 @@ struct AxShape {
 // phase `phase`; D: the NQ x NQ derivative matrix (anything indexable).
 // Returns false if the slab copy timed out (status set, copies drained).  In
 // CG mode, *part receives this thread's partial of <p, A_local p> (in T).
-template <int NQ, int EPB, typename T, typename GT, bool CG, typename DSrc>
+template <int NQ, int EPB, typename T, typename GT, bool CG, typename DSrc, bool PRE = false>
 __device__ __forceinline__ bool ax_group(const T *x, T *y, T *p, const GT *G, const DSrc &D, T beta,
                                          int64_t e0, int ne, T *regA, uint64_t *bar, uint32_t phase,
-                                         int32_t *status, T *part) {
+                                         int32_t *status, T *part, const T *dinv = nullptr) {
     using S = AxShape<NQ, EPB, T>;
     constexpr int NQ2 = S::NQ2, NP = S::NP;
     T *regB = regA + S::SLAB;
@@ -137,7 +138,9 @@ __device__ __forceinline__ bool ax_group(const T *x, T *y, T *p, const GT *G, co
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const int q = eb * NP + k * NQ2 + ij;
-                const T pn = fma(beta, s2[q], s1[q]);
+                // PCG: p = M^-1 r + beta p with the Jacobi M
+                const T zq = PRE ? dinv[nb + k * NQ2 + ij] * s1[q] : s1[q];
+                const T pn = fma(beta, s2[q], zq);
                 s2[q] = pn;
                 xk[k] = pn;
                 p[nb + k * NQ2 + ij] = pn;
@@ -209,7 +212,7 @@ struct ParamD {
     __device__ __forceinline__ T operator[](int q) const { return a.D[q]; }
 };
 
-template <int NQ, int EPB, typename T, typename GT, bool CG>
+template <int NQ, int EPB, typename T, typename GT, bool CG, bool PRE = false>
 __global__ void __launch_bounds__(AxShape<NQ, EPB, T>::NT)
 ax_kernel(const AxArgs<T, GT> P) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -226,7 +229,8 @@ ax_kernel(const AxArgs<T, GT> P) {
     const T beta = CG ? T(P.st->beta) : T(0);
     T part = T(0);
     const ParamD<T, GT> D{P};
-    if (!ax_group<NQ, EPB, T, GT, CG>(P.x, P.y, P.p, P.G, D, beta, e0, ne, regA, bar, 0u, P.status, &part))
+    if (!ax_group<NQ, EPB, T, GT, CG, ParamD<T, GT>, PRE>(P.x, P.y, P.p, P.G, D, beta, e0, ne, regA, bar, 0u,
+                                                         P.status, &part, P.dinv))
         return;
     if (CG) {
         // the column's partial is formed in T; the block and grid sums are FP64
@@ -251,13 +255,13 @@ struct AxEpb {
     static constexpr int value = sizeof(T) == 8 ? f64 : f32;
 };
 
-template <int NQ, typename T, typename GT, bool CG>
+template <int NQ, typename T, typename GT, bool CG, bool PRE = false>
 static int ax_attr() {
     constexpr int EPB = AxEpb<NQ, T>::value;
     using S = AxShape<NQ, EPB, T>;
     static bool attr_set = false;
     if (!attr_set) {
-        const int rc = cuda_check(cudaFuncSetAttribute(ax_kernel<NQ, EPB, T, GT, CG>,
+        const int rc = cuda_check(cudaFuncSetAttribute(ax_kernel<NQ, EPB, T, GT, CG, PRE>,
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::SMEM)),
                                   "ax: smem attribute");
         if (rc != SEM_OK) return rc;
@@ -266,31 +270,31 @@ static int ax_attr() {
     return SEM_OK;
 }
 
-template <int NQ, typename T, typename GT, bool CG>
+template <int NQ, typename T, typename GT, bool CG, bool PRE = false>
 static int launch_ax_nq(const Problem *Pb, const AxArgs<T, GT> &a) {
     constexpr int EPB = AxEpb<NQ, T>::value;
     using S = AxShape<NQ, EPB, T>;
-    const int arc = ax_attr<NQ, T, GT, CG>();
+    const int arc = ax_attr<NQ, T, GT, CG, PRE>();
     if (arc != SEM_OK) return arc;
     const int64_t blocks = (Pb->E + EPB - 1) / EPB;
     if (CG && blocks > kMaxPartials) return set_error(SEM_ERANGE, "ax: too many elements for one launch");
-    ax_kernel<NQ, EPB, T, GT, CG><<<unsigned(blocks), S::NT, S::SMEM, stream()>>>(a);
+    ax_kernel<NQ, EPB, T, GT, CG, PRE><<<unsigned(blocks), S::NT, S::SMEM, stream()>>>(a);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "ax_kernel");
 }
 
-template <typename T, typename GT, bool CG>
+template <typename T, typename GT, bool CG, bool PRE = false>
 static int launch_ax_any(const Problem *Pb, const AxArgs<T, GT> &a) {
     switch (Pb->nq) {
-        case 2: return launch_ax_nq<2, T, GT, CG>(Pb, a);
-        case 3: return launch_ax_nq<3, T, GT, CG>(Pb, a);
-        case 4: return launch_ax_nq<4, T, GT, CG>(Pb, a);
-        case 5: return launch_ax_nq<5, T, GT, CG>(Pb, a);
-        case 6: return launch_ax_nq<6, T, GT, CG>(Pb, a);
-        case 7: return launch_ax_nq<7, T, GT, CG>(Pb, a);
-        case 8: return launch_ax_nq<8, T, GT, CG>(Pb, a);
-        case 9: return launch_ax_nq<9, T, GT, CG>(Pb, a);
-        case 10: return launch_ax_nq<10, T, GT, CG>(Pb, a);
+        case 2: return launch_ax_nq<2, T, GT, CG, PRE>(Pb, a);
+        case 3: return launch_ax_nq<3, T, GT, CG, PRE>(Pb, a);
+        case 4: return launch_ax_nq<4, T, GT, CG, PRE>(Pb, a);
+        case 5: return launch_ax_nq<5, T, GT, CG, PRE>(Pb, a);
+        case 6: return launch_ax_nq<6, T, GT, CG, PRE>(Pb, a);
+        case 7: return launch_ax_nq<7, T, GT, CG, PRE>(Pb, a);
+        case 8: return launch_ax_nq<8, T, GT, CG, PRE>(Pb, a);
+        case 9: return launch_ax_nq<9, T, GT, CG, PRE>(Pb, a);
+        case 10: return launch_ax_nq<10, T, GT, CG, PRE>(Pb, a);
         default: return set_error(SEM_EARG, "ax: unsupported order");
     }
 }
@@ -302,6 +306,7 @@ static int prepare_ax_any(const Problem *Pb) {
 #define SEM_PREP(Q)                                      \
     case Q:                                              \
         rc = ax_attr<Q, T, GT, false>();                 \
+        if (rc == SEM_OK) rc = ax_attr<Q, T, GT, true, true>();   \
         return rc != SEM_OK ? rc : ax_attr<Q, T, GT, true>();
         SEM_PREP(2) SEM_PREP(3) SEM_PREP(4) SEM_PREP(5) SEM_PREP(6)
         SEM_PREP(7) SEM_PREP(8) SEM_PREP(9) SEM_PREP(10)

@@ -144,9 +144,10 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
 // Same sums as update_node: for each (t, s) choice in ascending element
 // order, the r-face neighbour (node i = 0 only, lower element) comes before
 // the own value and the other r-face neighbour (node i = N only) after it.
-template <int NQ, int V, typename T, typename Acc>
+template <int NQ, int V, typename T, typename Acc, bool PRE = false>
 __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                         const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha) {
+                                         const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha,
+                                         const T *__restrict__ dinv = nullptr, Acc *acc_rr = nullptr) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
     const unsigned e = unsigned(l0) / unsigned(NP);
     const int q = l0 - int(e) * NP;
@@ -187,7 +188,9 @@ __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, 
     vload<T, V>(x + l0, xv);
     vload<T, V>(p + l0, pv);
     vload<T, V>(r + l0, rv);
-    Acc acc = Acc(0);
+    Acc acc = Acc(0), rr = Acc(0);
+    T dv[V];
+    if (PRE) vload<T, V>(dinv + l0, dv);
     const bool owner_row = sy >= 0 && sz >= 0;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -208,11 +211,20 @@ __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, 
         if (!masked) {
             xv[v] = fma(alpha, pv[v], xv[v]);
             rv[v] = fma(-alpha, T(s), rv[v]);
-            if (owner_row && !first_lo) acc = fma(Acc(rv[v]), Acc(rv[v]), acc);
+            if (owner_row && !first_lo) {
+                if (PRE) {
+                    // <r, M^-1 r> for beta and <r, r> for the stop test
+                    acc = fma(Acc(rv[v]), Acc(dv[v] * rv[v]), acc);
+                    rr = fma(Acc(rv[v]), Acc(rv[v]), rr);
+                } else {
+                    acc = fma(Acc(rv[v]), Acc(rv[v]), acc);
+                }
+            }
         }
     }
     vstore<T, V>(x + l0, xv);
     vstore<T, V>(r + l0, rv);
+    if (PRE) *acc_rr += rr;
     return acc;
 }
 

@@ -172,6 +172,51 @@ __device__ __forceinline__ double finish_partials(const double *partials, int n,
     return acc;
 }
 
+// Two-value variants (PCG: <r, z> and <r, r>): slots partials[2b], [2b+1].
+__device__ __forceinline__ bool publish_partial2(double v0, double v1, double *partials, uint32_t *ticket) {
+    __shared__ int s_last2;
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = v0;
+        partials[2 * blockIdx.x + 1] = v1;
+        __threadfence();
+        const uint32_t t = atomicAdd(ticket, 1u);
+        s_last2 = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return s_last2 != 0;
+}
+
+__device__ __forceinline__ void finish_partials2(const double *partials, int n, uint32_t *ticket, double *sbuf,
+                                                 double *t0, double *t1) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        a += __ldcg(partials + 2 * q);
+        b += __ldcg(partials + 2 * q + 1);
+    }
+    a = block_sum(a, sbuf);
+    b = block_sum(b, sbuf);
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
+        *t0 = a;
+        *t1 = b;
+    }
+}
+
+// Closing step of a PCG iteration (thread 0 of the last block): rho_new =
+// <r, M^-1 r> drives beta, rr = <r, r> the stop test sqrt(rr / bb) <= tol.
+__device__ __forceinline__ void pcg_close_iteration(CgState *st, double rho_new, double rr) {
+    const int it = st->iter + 1;
+    st->iter = it;
+    st->rr = rr;
+    if (st->hist) st->hist[it] = sqrt(rr);
+    const double rho = st->rho;
+    st->beta = rho_new / rho;
+    st->rho = rho_new;
+    const bool conv = st->tol > 0.0 && sqrt(rr / st->bb) <= st->tol;
+    if (conv || it >= st->maxit) st->done = 1;
+}
+
 // Closing step of a CG iteration, run by thread 0 of the last block once
 // rho_new = <r_{k+1}, r_{k+1}> is known: iteration count, optional history,
 // beta = rho_new / rho, and the stop flag (relative residual or maxit).

@@ -33,7 +33,8 @@ struct CgState {
     double pap;        // <p, A p>
     double tol;        // stop when sqrt(rho/rho0) <= tol (tol <= 0: never)
     double dot_out;    // result slot of the "dot" kernel
-    double spare;
+    double rr;         // PCG: <r_k, r_k> (the stop test uses sqrt(rr / bb))
+    double bb;         // PCG: <b, b>
     double *hist;      // optional: hist[k] = sqrt(rho_k)
     int32_t iter;
     int32_t maxit;
@@ -66,11 +67,13 @@ struct Problem {
     int32_t *sh_ptr = nullptr, *sh_idx = nullptr;
     int64_t n_sh = 0, n_sh_copies = 0;
     // Dirichlet mask: local indices on the cube boundary
-    int32_t *msk_idx = nullptr;
+    int32_t *msk_idx = nullptr;  // local indices on the cube boundary
     int64_t n_mask = 0;
 
     // CG work vectors and state
     double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr;
+    double *dinv = nullptr;        // Jacobi: 1 / diag(A) (0 on masked nodes), on first PCG use
+    cudaGraphExec_t graph_pcg = nullptr;
     double *partials = nullptr;
     CgState *st = nullptr;
     CgState *st_host = nullptr;    // pinned mirror for polling
@@ -134,6 +137,10 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
 int launch_cg_update(const Problem *P);
 int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, double *hist,
              int64_t *iters, double *rel_res);
+int launch_ax_pcg(const Problem *P);         // p = dinv r + beta p; w = A_local p; <p,w>
+int jacobi_prepare(Problem *P);              // dinv = 1 / (mask(QQ^T diag(A_local)))
+int pcg_solve(Problem *P, const double *b, double *x, double tol, int maxit, double *hist,
+              int64_t *iters, double *rel_res);
 
 // ---- batches (sem_batch.cu) -------------------------------------------------
 struct Batch;

@@ -413,6 +413,8 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
 void problem_destroy(Problem *P) {
     if (!P) return;
     if (P->graph) cudaGraphExecDestroy(P->graph);
+    if (P->graph_pcg) cudaGraphExecDestroy(P->graph_pcg);
+    if (P->dinv) dev_free(P->dinv);
     mixed_release(P);
     double *dptrs[] = {P->verts, P->G, P->B, P->c, P->x, P->r, P->p, P->w, P->partials};
     for (double *q : dptrs)

@@ -83,6 +83,15 @@ class Mesh:
                 int(inner_maxit), int(gprec), i, o, r, hist_outer)
         return i.value, o.value, r.value
 
+    def pcg_solve(self, b, x, tol: float, maxit: int, hist=None):
+        """Jacobi-preconditioned CG; returns (iters, ||r||_c / ||b||_c)."""
+        it, res = sem.OutInt(), sem.OutDouble()
+        sem.run("pcg_solve", self.handle, b, x, float(tol), int(maxit), it, res, hist)
+        return it.value, res.value
+
+    def jacobi(self, dinv):
+        sem.run("jacobi", self.handle, dinv)
+
     def true_res(self, b, x) -> float:
         o = sem.OutDouble()
         sem.run("true_res", self.handle, b, x, o)
