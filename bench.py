@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--inner-tol", type=float, default=1e-3, help="inner FP32 CG residual reduction")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
@@ -281,6 +282,28 @@ def run_ours(a):
                 "peak_note": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 2 DFMA/clk x "
                              "2 flop x 2.07 GHz); fp64_probe_gflops is the same pipe measured live"}
 
+    # ---- Jacobi-preconditioned CG (FP64), the original Nekbone method
+    pcg = None
+    if not a.no_pcg:
+        xp = torch.empty_like(b)
+        M.pcg_solve(b, xp, a.tol, a.maxit)   # warm-up: preconditioner and graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        itp = 0
+        for _ in range(a.steps):
+            it_p, rel_p = M.pcg_solve(b, xp, a.tol, a.maxit)
+            itp += it_p
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1) / a.steps
+        pcg = {"workload": "same problem, Jacobi-preconditioned FP64 CG to the same tolerance",
+               "ms_per_solve": ms_p, "iters_per_solve": itp // a.steps,
+               "gdofs": E * N ** 3 * (itp // a.steps) / (ms_p * 1e-3) / 1e9,
+               "speedup_solves_vs_cg": (t_max / a.steps) / ms_p, "rel_res": rel_p,
+               "rel_res_true": M.true_res(b, xp),
+               "err_vs_fp64_cg_inf": float((xp - x).abs().max().item() / x.abs().max().item())}
+
     # ---- mixed precision: FP32 inner CG (BF16 geometric factors), FP64 refinement
     mixed = None
     if not a.no_mixed:
@@ -342,7 +365,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "mixed": mixed, "batched": batched,
+                "pcg": pcg, "mixed": mixed, "batched": batched,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
