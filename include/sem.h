@@ -188,6 +188,30 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               inner iterations (modes 1, 2); rel_res: recursive (mode 0) or
  *               true (modes 1, 2) relative residual at exit.
  *   "batch_free" batch
+ *   "serve_open" capacity, budget_gb, mode, tol, inner_tol, K, maxit, OUT server
+ *               A solve server with continuous batching: at most `capacity`
+ *               solves active at once, their device memory within budget_gb;
+ *               mode as in batch_solve; K CG iterations per round.
+ *   "serve_submit" server, nx, ny, nz, N, verts (HOST double[(nx+1)(ny+1)(nz+1)*3]),
+ *               b (HOST double[nL]), assemble, arrival_s, OUT ticket
+ *               Queue a request (copied; no device work).  assemble = 0: b is
+ *               the right-hand side; 1: b is a nodal source f and the server
+ *               forms mask(QQ^T f) on admission.  arrival_s is the arrival
+ *               time on the server clock ("serve_now"), from which the latency
+ *               is measured.
+ *   "serve_step" server, OUT n_queued, OUT n_active, OUT n_completed
+ *               Admit queued requests in arrival order within the limits,
+ *               run one round of every active solve (requests that joined
+ *               start, running ones continue), retire finished ones (result
+ *               kept on the device until fetched).
+ *   "serve_result" server, ticket, [x: HOST or device double[nL]], OUT state,
+ *               OUT iters, OUT rel_res, OUT latency_ms
+ *               state 0 queued, 1 active, 2 done; when done, x receives the
+ *               solution and the request is released.
+ *   "serve_now" server, OUT seconds       the server clock
+ *   "serve_drain" server, tickets (HOST int64[cap]), cap, OUT n
+ *               tickets completed since the last drain (at most cap)
+ *   "serve_close" server
  * Unknown names return SEM_EKERNEL; wrong argument counts or kinds SEM_EARG. */
 int sem_run(const char *kernel, int nargs, const sem_arg *args);
 

@@ -6,4 +6,4 @@
 ``build``  -- compiles libsem.so in-tree for sm_103a
 """
 from . import inputs, sem  # noqa: F401  (sem loads libsem.so lazily, on first call)
-from .mesh import Batch, Mesh  # noqa: F401
+from .mesh import Batch, Mesh, Server  # noqa: F401

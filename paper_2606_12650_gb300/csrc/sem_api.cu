@@ -42,6 +42,7 @@ struct Context {
     std::map<uintptr_t, Mirror> mirrors;
     std::map<int64_t, Problem *> problems;
     std::map<int64_t, Batch *> batches;
+    std::map<int64_t, Server *> servers;
     int64_t next_handle = 1;
     int32_t *status_dev = nullptr;
     int32_t *status_pinned = nullptr;
@@ -235,13 +236,20 @@ struct ArgReader {
     }
 };
 
-Problem *get_problem(ArgReader &R, int k) {
+Problem *get_problem(ArgReader &R, int k, bool need_maps = true) {
     const int64_t h = R.i(k, "handle");
     if (R.err) return nullptr;
     auto it = g.problems.find(h);
     if (it == g.problems.end()) {
         R.fail(SEM_EHANDLE, "unknown problem handle " + std::to_string(h));
         return nullptr;
+    }
+    if (need_maps) {
+        const int rc = problem_maps(it->second);
+        if (rc != SEM_OK) {
+            R.err = rc;
+            return nullptr;
+        }
     }
     return it->second;
 }
@@ -346,7 +354,7 @@ int run_dot(ArgReader &R) {
 
 int run_geom(ArgReader &R) {
     if (!R.need(3)) return R.err;
-    Problem *P = get_problem(R, 0);
+    Problem *P = get_problem(R, 0, false);
     if (R.err) return R.err;
     double *G = static_cast<double *>(R.arr(1, size_t(P->nL) * 6 * sizeof(double), "G"));
     double *B = static_cast<double *>(R.arr(2, size_t(P->nL) * sizeof(double), "B"));
@@ -361,7 +369,7 @@ int run_geom(ArgReader &R) {
 
 int run_nodes(ArgReader &R) {
     if (!R.need(2)) return R.err;
-    Problem *P = get_problem(R, 0);
+    Problem *P = get_problem(R, 0, false);
     if (R.err) return R.err;
     double *X = static_cast<double *>(R.arr(1, size_t(P->nL) * 3 * sizeof(double), "X"));
     if (R.err) return R.err;
@@ -427,7 +435,7 @@ int run_cg_solve(ArgReader &R) {
 
 int run_ax32(ArgReader &R) {
     if (!R.need(4)) return R.err;
-    Problem *P = get_problem(R, 0);
+    Problem *P = get_problem(R, 0, false);
     if (R.err) return R.err;
     const size_t vb = size_t(P->nL) * sizeof(float);
     const float *x = static_cast<const float *>(R.arr(1, vb, "x"));
@@ -441,7 +449,7 @@ int run_ax32(ArgReader &R) {
 
 int run_cg_ax32(ArgReader &R) {
     if (!R.need(2)) return R.err;
-    Problem *P = get_problem(R, 0);
+    Problem *P = get_problem(R, 0, false);
     const int64_t gprec = R.i(1, "gprec");
     if (R.err) return R.err;
     int rc = mixed_prepare(P, int(gprec));
@@ -572,9 +580,130 @@ int run_batch_free(ArgReader &R) {
     return SEM_OK;
 }
 
+Server *get_server(ArgReader &R, int k) {
+    const int64_t h = R.i(k, "server");
+    if (R.err) return nullptr;
+    auto it = g.servers.find(h);
+    if (it == g.servers.end()) {
+        R.fail(SEM_EHANDLE, "unknown server handle " + std::to_string(h));
+        return nullptr;
+    }
+    return it->second;
+}
+
+int run_serve_open(ArgReader &R) {
+    if (!R.need(8)) return R.err;
+    const int64_t cap = R.i(0, "capacity");
+    const double budget = R.d(1, "budget_gb");
+    const int64_t mode = R.i(2, "mode");
+    const double tol = R.d(3, "tol");
+    const double inner_tol = R.d(4, "inner_tol");
+    const int64_t K = R.i(5, "K");
+    const int64_t maxit = R.i(6, "maxit");
+    int64_t *out = static_cast<int64_t *>(R.out(7, SEM_ARG_OUT_INT, "server"));
+    if (R.err) return R.err;
+    if (maxit < 1 || maxit > (1 << 30)) return R.fail(SEM_EARG, "maxit must be in [1, 2^30]");
+    Server *S = nullptr;
+    const int rc = serve_open(int(cap), budget, int(mode), tol, inner_tol, int(K), int(maxit), &S);
+    if (rc != SEM_OK) return rc;
+    const int64_t h = g.next_handle++;
+    g.servers[h] = S;
+    *out = h;
+    return SEM_OK;
+}
+
+int run_serve_submit(ArgReader &R) {
+    if (!R.need(10)) return R.err;
+    Server *S = get_server(R, 0);
+    const int64_t nx = R.i(1, "nx"), ny = R.i(2, "ny"), nz = R.i(3, "nz"), N = R.i(4, "N");
+    if (R.err) return R.err;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096 || N < 1 || N > 9)
+        return R.fail(SEM_EARG, "nx, ny, nz must be in [1, 4096] and N in [1, 9]");
+    const size_t nv = size_t(nx + 1) * size_t(ny + 1) * size_t(nz + 1) * 3;
+    const size_t nL = size_t(nx) * ny * nz * (N + 1) * (N + 1) * (N + 1);
+    const double *verts = static_cast<const double *>(R.host(5, nv * 8, "verts"));
+    const double *b = static_cast<const double *>(R.host(6, nL * 8, "b"));
+    const int64_t assemble = R.i(7, "assemble");
+    const double arrival = R.d(8, "arrival_s");
+    int64_t *ticket = static_cast<int64_t *>(R.out(9, SEM_ARG_OUT_INT, "ticket"));
+    if (R.err) return R.err;
+    return serve_submit(S, int(nx), int(ny), int(nz), int(N), verts, b, assemble != 0, arrival, ticket);
+}
+
+int run_serve_drain(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    Server *S = get_server(R, 0);
+    const int64_t cap = R.i(2, "cap");
+    if (R.err) return R.err;
+    if (cap < 0) return R.fail(SEM_EARG, "cap must be >= 0");
+    int64_t *out = static_cast<int64_t *>(R.host(1, size_t(cap) * 8, "tickets"));
+    int64_t *n = static_cast<int64_t *>(R.out(3, SEM_ARG_OUT_INT, "n"));
+    if (R.err) return R.err;
+    *n = serve_drain(S, out, cap);
+    return SEM_OK;
+}
+
+int run_serve_step(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    Server *S = get_server(R, 0);
+    int64_t *o1 = static_cast<int64_t *>(R.out(1, SEM_ARG_OUT_INT, "queued"));
+    int64_t *o2 = static_cast<int64_t *>(R.out(2, SEM_ARG_OUT_INT, "active"));
+    int64_t *o3 = static_cast<int64_t *>(R.out(3, SEM_ARG_OUT_INT, "completed"));
+    if (R.err) return R.err;
+    return serve_step(S, o1, o2, o3);
+}
+
+int run_serve_result(ArgReader &R) {
+    if (!R.need(7)) return R.err;
+    Server *S = get_server(R, 0);
+    const int64_t ticket = R.i(1, "ticket");
+    if (R.err) return R.err;
+    double *x = nullptr;
+    bool on_dev = false;
+    if (R.nargs > 2 && R.args[2].kind != SEM_ARG_NONE) {
+        const int64_t nL = serve_nodes_of(S, ticket);
+        if (nL < 0) return R.fail(SEM_EHANDLE, "unknown ticket");
+        if (R.args[2].kind == SEM_ARG_HOST) {
+            x = static_cast<double *>(R.host(2, size_t(nL) * 8, "x"));
+        } else {
+            x = static_cast<double *>(R.arr(2, size_t(nL) * 8, "x"));
+            on_dev = true;
+        }
+    }
+    int64_t *st = static_cast<int64_t *>(R.out(3, SEM_ARG_OUT_INT, "state"));
+    int64_t *its = static_cast<int64_t *>(R.out(4, SEM_ARG_OUT_INT, "iters"));
+    double *res = static_cast<double *>(R.out(5, SEM_ARG_OUT_DOUBLE, "rel_res"));
+    double *lat = static_cast<double *>(R.out(6, SEM_ARG_OUT_DOUBLE, "latency_ms"));
+    if (R.err) return R.err;
+    *its = 0;
+    *res = 0.0;
+    *lat = 0.0;
+    return serve_result(S, ticket, x, on_dev, st, its, res, lat);
+}
+
+int run_serve_now(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    Server *S = get_server(R, 0);
+    double *o = static_cast<double *>(R.out(1, SEM_ARG_OUT_DOUBLE, "seconds"));
+    if (R.err) return R.err;
+    *o = serve_now(S);
+    return SEM_OK;
+}
+
+int run_serve_close(ArgReader &R) {
+    if (!R.need(1)) return R.err;
+    const int64_t h = R.i(0, "server");
+    if (R.err) return R.err;
+    auto it = g.servers.find(h);
+    if (it == g.servers.end()) return R.fail(SEM_EHANDLE, "unknown server handle");
+    serve_close(it->second);
+    g.servers.erase(it);
+    return SEM_OK;
+}
+
 int run_cg_ax(ArgReader &R) {
     if (!R.need(1)) return R.err;
-    Problem *P = get_problem(R, 0);
+    Problem *P = get_problem(R, 0, false);
     if (R.err) return R.err;
     // clear the stop flag a finished solve leaves behind, so the kernel does its work
     const int rc = cuda_check(cudaMemsetAsync(&P->st->done, 0, sizeof(int32_t), g.cur_stream), "cg_ax: flag");
@@ -786,6 +915,13 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "batch_info") rc = run_batch_info(R);
     else if (k == "batch_solve") rc = run_batch_solve(R);
     else if (k == "batch_free") rc = run_batch_free(R);
+    else if (k == "serve_open") rc = run_serve_open(R);
+    else if (k == "serve_submit") rc = run_serve_submit(R);
+    else if (k == "serve_step") rc = run_serve_step(R);
+    else if (k == "serve_result") rc = run_serve_result(R);
+    else if (k == "serve_now") rc = run_serve_now(R);
+    else if (k == "serve_drain") rc = run_serve_drain(R);
+    else if (k == "serve_close") rc = run_serve_close(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
     else return set_error(SEM_EKERNEL, "sem_run: unknown kernel '" + k + "'");
     return rc;
@@ -801,6 +937,8 @@ int sem_sync(void) {
 int sem_finalize(void) {
     if (!g.up) return set_error(SEM_EINIT, "sem_finalize: not initialised");
     cudaStreamSynchronize(g.cur_stream);
+    for (auto &kv : g.servers) serve_close(kv.second);
+    g.servers.clear();
     for (auto &kv : g.batches) batch_destroy(kv.second);
     g.batches.clear();
     for (auto &kv : g.problems) problem_destroy(kv.second);

@@ -15,8 +15,14 @@
 // batch, so a problem's iterates are bit-identical alone or in any mix.
 //
 // States.  Each problem has its own CG state (and an inner one for mixed
-// precision); finished problems turn their items into no-ops, and a device
-// counter of finished problems is polled once per graph replay.
+// precision) and a few flags: `init` (start its solve this round), `refine`
+// (mixed precision: its inner solve ended, so the FP64 correction, residual
+// and restart run this round), `finished`.  Problems can join between rounds
+// (continuous batching); finished ones are reported through a device list and
+// their items become no-ops.  One round = the init phase for joining
+// problems, K CG iterations replayed from a CUDA graph, and (mixed) the
+// refinement phase for problems whose inner solve stopped -- each problem
+// refines as soon as its own inner solve ends, not in lockstep.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -39,19 +45,22 @@ constexpr int kVecItemNodes = 4096;
 struct BatchProb {
     int nq, nx, ny, nz;
     int64_t E, nL;
-    int64_t off;                    // offset in the concatenated b / x arrays
     const double *G;
     const __nv_bfloat16 *G16;
     const float *G32;
-    const double *c;
     double *x, *r, *p, *w;          // FP64 CG vectors / refinement x, r
     float *d32, *r32, *p32, *w32;   // inner (FP32) CG vectors
     CgState *st, *st_in;
+    const double *b;                // right-hand side
     int ax_first, ax_count;         // operator items
     int vec_first, vec_count;       // vector items
-    int32_t outer_done;             // mixed: true residual reached tol
+    int32_t init;                   // host sets: start this problem's solve next round
+    int32_t refine;                 // mixed: inner solve ended, refine this round
+    int32_t outer_done;             // mixed: true residual reached tol (or out of steps)
+    int32_t finished;               // solve over; reported once in the finished list
     int32_t inner_total;            // mixed: inner iterations so far
-    double bb;                      // <b, b>_c
+    int32_t outer_steps;            // mixed: refinement steps so far
+    double bb;                      // <b, b>
     double res;                     // mixed: current true relative residual
 };
 
@@ -70,29 +79,32 @@ enum BatchQ : int { kQAx = 0, kQVec = 1, kNumQ = 2 };
 
 struct BatchCtl {
     BatchQueue q[kNumQ];
-    unsigned n_done;                // problems whose (inner) CG finished
-    unsigned n_outer_done;          // mixed: problems whose true residual reached tol
-    unsigned pad[2];
+    unsigned n_finished;            // entries in the finished list
+    unsigned pad[3];
 };
 
 struct Batch {
+    int mode = 0;                   // 0 FP64 CG, 1 mixed (BF16 G), 2 mixed (FP32 G)
+    int K = 16;                     // CG iterations per round
+    double tol = 1e-8, inner_tol = 1e-3;
+    int maxit = 100000, max_outer = 50;
     std::vector<Problem *> probs;
-    std::vector<int64_t> offs;
-    int64_t nL_total = 0;
     int n_ax = 0, n_vec = 0;
+    int cap_probs = 0, cap_ax = 0, cap_vec = 0;
     BatchProb *d_probs = nullptr;
     BatchItem *d_ax = nullptr, *d_vec = nullptr;
     double *part = nullptr;         // one slot per item
     uint32_t *tickets = nullptr;    // per problem: [ax, vec]
+    int32_t *finished_ids = nullptr;
     BatchCtl *ctl = nullptr;
     BatchCtl *ctl_host = nullptr;
+    unsigned seen_finished = 0;
+    bool any_init = false;
     int grid_ax64 = 0, grid_ax32 = 0, grid_vec = 0;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // FP64 CG, inner bf16, inner f32
-    int graph_iters = 0;
+    cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
 };
 
-// ------------------------------------------------------------------ shapes
 template <int NQ>
 struct BEpb {
     static constexpr int value = kBatchThreads / (NQ * NQ);
@@ -208,8 +220,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
         const BatchItem item = items[it];
         BatchProb &P = probs[item.prob];
         CgState *st = MODE == 2 ? P.st_in : P.st;
-        if (CG && st->done) continue;
-        if (MODE == 1 && P.outer_done) continue;   // refinement: converged problems need no residual
+        if (CG && (st->done || P.finished)) continue;
+        if (MODE == 1 && !P.refine) continue;      // refinement residual: refining problems only
         const T beta = CG ? T(st->beta) : T(0);
         const T *xin;
         T *yout, *pv;
@@ -250,19 +262,19 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
 enum VecMode : int {
     kVecUpdate64 = 0,   // FP64 CG update (gs of w, x/r update, <r,r>, close)
     kVecUpdate32 = 1,   // FP32 inner CG update
-    kVecInit64 = 2,     // x = 0, p = 0, r = b, <b,b> -> CG state
-    kVecInner = 3,      // r32 = r, d32 = p32 = 0, <r32,r32> -> inner state
-    kVecCorrect = 4,    // x += d32
-    kVecResidual = 5,   // r = b - mask(QQ^T w), <r,r> -> outer test
-    kVecCopyOut = 6,    // xout = x
+    kVecInit64 = 2,     // joining problems: x = 0, p = 0, r = b, <b,b>
+    kVecInner = 3,      // joining or refining problems: r32 = r, d32 = p32 = 0, inner state
+    kVecCorrect = 4,    // refining problems: x += d32
+    kVecResidual = 5,   // refining problems: r = b - mask(QQ^T w), <r,r>, outer test
 };
 
 struct VecArgs {
-    const double *b_all;
-    double *x_all;
-    double tol;         // outer tolerance (residual test), or CG tolerance (init)
-    double inner_tol;   // minimum inner reduction (mixed)
-    int maxit;
+    int mode;           // solve kind (0 FP64 CG, 1/2 mixed)
+    int maxit;          // CG (or inner CG) iteration limit
+    int max_outer;      // mixed: refinement step limit
+    int pad;
+    double tol;         // relative residual target
+    double inner_tol;   // mixed: minimum inner reduction
 };
 
 // r = b - mask(QQ^T w) at one node (box-structured copies, ascending order),
@@ -294,8 +306,7 @@ __device__ __forceinline__ double residual_node(double *r, const double *b, cons
 }
 
 template <int NQ, int MODE>
-__device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, const VecArgs &A, int64_t first,
-                                                int count) {
+__device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, int64_t first, int count) {
     double acc = 0.0;
     const int tid = threadIdx.x;
     if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
@@ -311,24 +322,23 @@ __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, const Ve
             a += update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, P.nx, P.ny, P.nz, alpha);
         acc = double(a);
     } else if (MODE == kVecInit64) {
-        const double *b = A.b_all + P.off;
+        // <b, b> over global nodes (each counted at its first copy)
         for (int v = tid; v < count; v += blockDim.x) {
             const int64_t l = first + v;
-            const double bl = b[l];
+            const double bl = P.b[l];
             P.x[l] = 0.0;
             P.p[l] = 0.0;
             P.r[l] = bl;
-            acc = fma(P.c[l] * bl, bl, acc);
+            if (box_node<NQ>(int(l), P.nx, P.ny, P.nz).owner) acc = fma(bl, bl, acc);
         }
     } else if (MODE == kVecInner) {
-        if (P.outer_done) return 0.0;   // converged: the inner state is closed in the handler
         for (int v = tid; v < count; v += blockDim.x) {
             const int64_t l = first + v;
             const float f = __double2float_rn(P.r[l]);
             P.r32[l] = f;
             P.d32[l] = 0.f;
             P.p32[l] = 0.f;
-            acc += P.c[l] * double(f) * double(f);
+            if (box_node<NQ>(int(l), P.nx, P.ny, P.nz).owner) acc += double(f) * double(f);
         }
     } else if (MODE == kVecCorrect) {
         for (int v = tid; v < count; v += blockDim.x) {
@@ -336,23 +346,41 @@ __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, const Ve
             P.x[l] += double(P.d32[l]);
         }
     } else if (MODE == kVecResidual) {
-        const double *b = A.b_all + P.off;
         for (int v = tid; v < count; v += blockDim.x)
-            acc += residual_node<NQ>(P.r, b, P.w, int(first) + v, P.nx, P.ny, P.nz);
-    } else if (MODE == kVecCopyOut) {
-        double *xo = A.x_all + P.off;
-        for (int v = tid; v < count; v += blockDim.x) xo[first + v] = P.x[first + v];
+            acc += residual_node<NQ>(P.r, P.b, P.w, int(first) + v, P.nx, P.ny, P.nz);
     }
     return acc;
+}
+
+// Mark a problem finished and append it to the finished list (thread 0).
+__device__ __forceinline__ void finish_problem(BatchProb &P, int prob, BatchCtl *ctl, int32_t *finished_ids) {
+    if (P.finished) return;
+    P.finished = 1;
+    const unsigned k = atomicAdd(&ctl->n_finished, 1u);
+    finished_ids[k] = prob;
+}
+
+__device__ __forceinline__ void init_state(CgState *st, double rho0, double tol, int maxit) {
+    st->rho = rho0;
+    st->rho0 = rho0;
+    st->alpha = st->beta = st->pap = 0.0;
+    st->tol = tol;
+    st->hist = nullptr;
+    st->iter = 0;
+    st->maxit = maxit;
+    st->done = (rho0 == 0.0 || maxit <= 0) ? 1 : 0;
+    st->ticket_ax = 0;
+    st->ticket_up = 0;
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(kBatchThreads, 3) batch_vec_kernel(BatchProb *probs, const BatchItem *items,
                                                                   int nitems, double *part, uint32_t *tickets,
-                                                                  BatchCtl *ctl, VecArgs A) {
+                                                                  BatchCtl *ctl, int32_t *finished_ids,
+                                                                  VecArgs A) {
     __shared__ double red[32];
     __shared__ int s_item;
-    constexpr bool REDUCES = MODE != kVecCorrect && MODE != kVecCopyOut;
+    constexpr bool REDUCES = MODE != kVecCorrect;
     BatchQueue *q = &ctl->q[kQVec];
     while (true) {
         const int it = next_item(q, &s_item);
@@ -360,17 +388,18 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_vec_kernel(BatchProb *
         const BatchItem item = items[it];
         BatchProb &P = probs[item.prob];
         CgState *st = (MODE == kVecUpdate32 || MODE == kVecInner) ? P.st_in : P.st;
-        // skip finished problems (their items are no-ops)
-        if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
-            if (st->done) continue;
-        } else if (MODE == kVecCorrect || MODE == kVecResidual) {
-            if (P.outer_done) continue;
-        }
+        // which problems take part in this phase
+        bool on;
+        if (MODE == kVecUpdate64 || MODE == kVecUpdate32) on = !st->done && !P.finished;
+        else if (MODE == kVecInit64) on = P.init != 0;
+        else if (MODE == kVecInner) on = (P.init || P.refine) && !P.outer_done;
+        else on = P.refine != 0;   // correct, residual
+        if (!on) continue;
         double acc = 0.0;
         switch (item.nq) {
-#define SEM_BV(Q)                                                          \
-    case Q:                                                                \
-        acc = vec_item_body<Q, MODE>(P, st, A, item.first, item.count);    \
+#define SEM_BV(Q)                                                  \
+    case Q:                                                        \
+        acc = vec_item_body<Q, MODE>(P, st, item.first, item.count); \
         break;
             SEM_BV(2) SEM_BV(3) SEM_BV(4) SEM_BV(5) SEM_BV(6) SEM_BV(7) SEM_BV(8) SEM_BV(9) SEM_BV(10)
 #undef SEM_BV
@@ -379,54 +408,47 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_vec_kernel(BatchProb *
         if (!REDUCES) continue;
         const double bs = block_sum(acc, red);
         double tot;
-        if (item_partial(bs, part, it, &tickets[2 * item.prob + 1], P.vec_first, P.vec_count, red, &tot) &&
-            threadIdx.x == 0) {
-            if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
-                cg_close_iteration(st, tot);
-                if (st->done) atomicAdd(&ctl->n_done, 1u);
-            } else if (MODE == kVecInit64) {
-                st->rho = tot;
-                st->rho0 = tot;
-                st->alpha = st->beta = st->pap = 0.0;
-                st->tol = A.tol;
-                st->hist = nullptr;
-                st->iter = 0;
-                st->maxit = A.maxit;
-                st->done = (tot == 0.0 || A.maxit <= 0) ? 1 : 0;
-                P.bb = tot;
-                P.res = tot > 0.0 ? 1.0 : 0.0;
-                P.outer_done = (tot == 0.0) ? 1 : 0;
-                P.inner_total = 0;
-                if (st->done) atomicAdd(&ctl->n_done, 1u);
-                if (P.outer_done) atomicAdd(&ctl->n_outer_done, 1u);
-            } else if (MODE == kVecInner) {
-                if (P.outer_done) {
-                    st->done = 1;   // not counted: only problems still refining are waited for
-                    st->iter = 0;
-                } else {
-                    const double eta = fmin(0.5, fmax(A.inner_tol, 0.5 * A.tol / P.res));
-                    st->rho = tot;
-                    st->rho0 = tot;
-                    st->alpha = st->beta = st->pap = 0.0;
-                    st->tol = eta;
-                    st->hist = nullptr;
-                    st->iter = 0;
-                    st->maxit = A.maxit;
-                    st->done = (tot == 0.0) ? 1 : 0;
-                    if (st->done) atomicAdd(&ctl->n_done, 1u);
-                }
-            } else if (MODE == kVecResidual) {
-                P.inner_total += P.st_in->iter;
-                P.res = P.bb > 0.0 ? sqrt(tot / P.bb) : 0.0;
-                P.st->rho = tot;
-                if (P.res <= A.tol) {
-                    P.outer_done = 1;
-                    atomicAdd(&ctl->n_outer_done, 1u);
-                }
+        if (!item_partial(bs, part, it, &tickets[2 * item.prob + 1], P.vec_first, P.vec_count, red, &tot) ||
+            threadIdx.x != 0)
+            continue;
+        if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
+            cg_close_iteration(st, tot);
+            if (MODE == kVecUpdate64 && st->done) finish_problem(P, item.prob, ctl, finished_ids);
+        } else if (MODE == kVecInit64) {
+            init_state(P.st, tot, A.mode == 0 ? A.tol : 0.0, A.maxit);
+            if (A.mode != 0) P.st_in->done = 1;   // no inner solve until kVecInner starts one
+            P.bb = tot;
+            P.res = tot > 0.0 ? 1.0 : 0.0;
+            P.outer_done = tot == 0.0 ? 1 : 0;
+            P.inner_total = 0;
+            P.outer_steps = 0;
+            P.refine = 0;
+            if (tot == 0.0) finish_problem(P, item.prob, ctl, finished_ids);
+        } else if (MODE == kVecInner) {
+            init_state(st, tot, fmin(0.5, fmax(A.inner_tol, 0.5 * A.tol / P.res)), A.maxit);
+        } else if (MODE == kVecResidual) {
+            P.inner_total += P.st_in->iter;
+            P.outer_steps += 1;
+            P.res = P.bb > 0.0 ? sqrt(tot / P.bb) : 0.0;
+            if (P.res <= A.tol || P.outer_steps >= A.max_outer) {
+                P.outer_done = 1;
+                finish_problem(P, item.prob, ctl, finished_ids);
             }
         }
     }
     leave_queue(q);
+}
+
+// Per-problem flag updates between phases (one thread per problem).
+enum FlagOp : int { kFlagClearInit = 0, kFlagMarkRefine = 1, kFlagClearRefine = 2 };
+
+__global__ void batch_flags_kernel(BatchProb *probs, int n, int op) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    BatchProb &P = probs[k];
+    if (op == kFlagClearInit) P.init = 0;
+    else if (op == kFlagMarkRefine) P.refine = (!P.finished && !P.outer_done && P.st_in->done) ? 1 : 0;
+    else P.refine = 0;
 }
 
 // ------------------------------------------------------------------ host side
@@ -443,18 +465,28 @@ static int batch_grid(const void *kern, size_t smem, int *out) {
 template <typename T, typename GT, int MODE>
 static int launch_bax(Batch *B, int grid) {
     constexpr size_t sm = batch_ax_smem<T>();
-    batch_ax_kernel<T, GT, MODE><<<unsigned(grid), kBatchThreads, sm, stream()>>>(
+    const int g = std::max(1, std::min(grid, B->n_ax));
+    batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(
         B->d_probs, B->d_ax, B->n_ax, B->part, B->tickets, B->ctl, status_word());
     count_launches(1);
     return cuda_check(cudaGetLastError(), "batch_ax_kernel");
 }
 
 template <int MODE>
-static int launch_bvec(Batch *B, const VecArgs &A) {
-    batch_vec_kernel<MODE><<<unsigned(B->grid_vec), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->n_vec,
-                                                                                B->part, B->tickets, B->ctl, A);
+static int launch_bvec(Batch *B) {
+    const VecArgs A{B->mode, B->maxit, B->max_outer, 0, B->tol, B->inner_tol};
+    const int g = std::max(1, std::min(B->grid_vec, B->n_vec));
+    batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->n_vec, B->part,
+                                                                       B->tickets, B->ctl, B->finished_ids, A);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "batch_vec_kernel");
+}
+
+static int launch_flags(Batch *B, int op) {
+    const int n = int(B->probs.size());
+    batch_flags_kernel<<<unsigned((n + 127) / 128), 128, 0, stream()>>>(B->d_probs, n, op);
+    count_launches(1);
+    return cuda_check(cudaGetLastError(), "batch_flags_kernel");
 }
 
 static int batch_attrs(Batch *B) {
@@ -467,11 +499,11 @@ static int batch_attrs(Batch *B) {
             gll_rule_and_derivative(N, xi, w, h64[N - 1]);
             for (int q = 0; q < (N + 1) * (N + 1); ++q) h32[N - 1][q] = float(h64[N - 1][q]);
         }
-        int rc0 = cuda_check(cudaMemcpyToSymbol(c_D64, h64, sizeof h64), "batch: D table");
-        if (rc0 == SEM_OK) rc0 = cuda_check(cudaMemcpyToSymbol(c_D32, h32, sizeof h32), "batch: D table");
-        if (rc0 != SEM_OK) return rc0;
+        int rc = cuda_check(cudaMemcpyToSymbol(c_D64, h64, sizeof h64), "batch: D table");
+        if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_D32, h32, sizeof h32), "batch: D table");
         const int a = int(batch_ax_smem<double>()), f = int(batch_ax_smem<float>());
-        int rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 0>,
+        if (rc == SEM_OK)
+            rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 0>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, a), "batch attr");
         if (rc == SEM_OK)
             rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 1>,
@@ -495,90 +527,17 @@ static int batch_attrs(Batch *B) {
     return rc;
 }
 
-int batch_create(Problem **probs, int n, Batch **out) {
-    *out = nullptr;
-    if (n < 1) return set_error(SEM_EARG, "batch: needs at least one problem");
-    Batch *B = new Batch();
-    B->probs.assign(probs, probs + n);
-    std::vector<BatchProb> hp(n);
-    std::vector<BatchItem> ax, vec;
-    int rc = SEM_OK;
-    int64_t off = 0;
-    for (int k = 0; k < n && rc == SEM_OK; ++k) {
-        Problem *P = probs[k];
-        rc = mixed_prepare(P, kGBF16);
-        if (rc == SEM_OK) rc = mixed_prepare(P, kGF32);
-        if (rc != SEM_OK) break;
-        BatchProb &q = hp[k];
-        memset(&q, 0, sizeof q);
-        q.nq = P->nq; q.nx = P->nx; q.ny = P->ny; q.nz = P->nz;
-        q.E = P->E; q.nL = P->nL; q.off = off;
-        q.G = P->G; q.G16 = static_cast<const __nv_bfloat16 *>(P->G16); q.G32 = static_cast<const float *>(P->G32);
-        q.c = P->c;
-        q.x = P->x; q.r = P->r; q.p = P->p; q.w = P->w;
-        q.d32 = P->d32; q.r32 = P->r32; q.p32 = P->p32; q.w32 = P->w32;
-        q.st = P->st; q.st_in = P->st_in;
-        const int epb = kBatchThreads / (P->nq * P->nq);
-        q.ax_first = int(ax.size());
-        for (int64_t e = 0; e < P->E; e += epb)
-            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(epb, P->E - e)), 0});
-        q.ax_count = int(ax.size()) - q.ax_first;
-        // vector items: row-aligned runs of about kVecItemNodes nodes
-        const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
-        q.vec_first = int(vec.size());
-        for (int64_t l = 0; l < P->nL; l += chunk)
-            vec.push_back(BatchItem{k, P->nq, l, int(std::min<int64_t>(chunk, P->nL - l)), 0});
-        q.vec_count = int(vec.size()) - q.vec_first;
-        B->offs.push_back(off);
-        off += P->nL;
-    }
-    B->nL_total = off;
-    B->n_ax = int(ax.size());
-    B->n_vec = int(vec.size());
-    if (rc == SEM_OK) {
-        B->d_probs = static_cast<BatchProb *>(dev_alloc(sizeof(BatchProb) * n));
-        B->d_ax = static_cast<BatchItem *>(dev_alloc(sizeof(BatchItem) * ax.size()));
-        B->d_vec = static_cast<BatchItem *>(dev_alloc(sizeof(BatchItem) * vec.size()));
-        B->part = static_cast<double *>(dev_alloc(sizeof(double) * std::max(ax.size(), vec.size())));
-        B->tickets = static_cast<uint32_t *>(dev_alloc(sizeof(uint32_t) * 2 * n));
-        B->ctl = static_cast<BatchCtl *>(dev_alloc(sizeof(BatchCtl)));
-        if (!B->d_probs || !B->d_ax || !B->d_vec || !B->part || !B->tickets || !B->ctl) rc = SEM_ENOMEM;
-    }
-    if (rc == SEM_OK)
-        rc = cuda_check(cudaMemcpyAsync(B->d_probs, hp.data(), sizeof(BatchProb) * n, cudaMemcpyHostToDevice, stream()),
-                        "batch: descriptors");
-    if (rc == SEM_OK)
-        rc = cuda_check(cudaMemcpyAsync(B->d_ax, ax.data(), sizeof(BatchItem) * ax.size(), cudaMemcpyHostToDevice,
-                                        stream()), "batch: items");
-    if (rc == SEM_OK)
-        rc = cuda_check(cudaMemcpyAsync(B->d_vec, vec.data(), sizeof(BatchItem) * vec.size(), cudaMemcpyHostToDevice,
-                                        stream()), "batch: items");
-    if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(B->tickets, 0, sizeof(uint32_t) * 2 * n, stream()), "batch");
-    if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(B->ctl, 0, sizeof(BatchCtl), stream()), "batch");
-    if (rc == SEM_OK) rc = cuda_check(cudaMallocHost(&B->ctl_host, sizeof(BatchCtl)), "batch: pinned");
-    if (rc == SEM_OK) rc = batch_attrs(B);
-    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
-    if (rc != SEM_OK) {
-        batch_destroy(B);
-        return rc;
-    }
-    *out = B;
+template <typename X>
+static int grow(X **buf, int *cap, int need) {
+    if (need <= *cap && *buf) return SEM_OK;
+    const int c = std::max(need, std::max(16, 2 * *cap));
+    X *nb = static_cast<X *>(dev_alloc(sizeof(X) * size_t(c)));
+    if (!nb) return SEM_ENOMEM;
+    if (*buf) dev_free(*buf);
+    *buf = nb;
+    *cap = c;
     return SEM_OK;
 }
-
-void batch_destroy(Batch *B) {
-    if (!B) return;
-    for (auto &g : B->graph)
-        if (g) cudaGraphExecDestroy(g);
-    void *ptrs[] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->ctl};
-    for (void *q : ptrs)
-        if (q) dev_free(q);
-    if (B->ctl_host) cudaFreeHost(B->ctl_host);
-    delete B;
-}
-
-int64_t batch_total_nodes(const Batch *B) { return B->nL_total; }
-int batch_size(const Batch *B) { return int(B->probs.size()); }
 
 static int read_ctl(Batch *B) {
     int rc = cuda_check(cudaMemcpyAsync(B->ctl_host, B->ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, stream()),
@@ -588,100 +547,219 @@ static int read_ctl(Batch *B) {
     return rc;
 }
 
-static int reset_done(Batch *B) {
-    return cuda_check(cudaMemsetAsync(&B->ctl->n_done, 0, sizeof(unsigned), stream()), "batch: reset");
+Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_outer, int K) {
+    Batch *B = new Batch();
+    B->mode = mode;
+    B->tol = tol;
+    B->maxit = maxit;
+    B->inner_tol = inner_tol;
+    B->max_outer = max_outer;
+    B->K = K;
+    return B;
 }
 
-// K iterations of (operator, update) for one precision, captured once.
-static int capture(Batch *B, int which) {
-    if (B->graph[which] && B->graph_stream == stream()) return SEM_OK;
-    if (B->graph[which]) {
-        cudaGraphExecDestroy(B->graph[which]);
-        B->graph[which] = nullptr;
+// Set the problems of the batch.  Problems already in the batch keep their
+// solve state; problems listed with start[k] != 0 (re)start their solve with
+// right-hand side b[k] at the next round.  Invalidates the captured graph.
+int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *start, int n) {
+    int rc = SEM_OK;
+    if (!B->ctl) {
+        B->ctl = static_cast<BatchCtl *>(dev_alloc(sizeof(BatchCtl)));
+        if (!B->ctl) return SEM_ENOMEM;
+        rc = cuda_check(cudaMemsetAsync(B->ctl, 0, sizeof(BatchCtl), stream()), "batch: control");
+        if (rc == SEM_OK) rc = cuda_check(cudaMallocHost(&B->ctl_host, sizeof(BatchCtl)), "batch: pinned");
+        if (rc == SEM_OK) rc = batch_attrs(B);
+        if (rc != SEM_OK) return rc;
     }
-    const int K = B->nL_total < (int64_t(1) << 22) ? 64 : 16;
-    cudaGraph_t g = nullptr;
-    int rc = cuda_check(cudaStreamBeginCapture(stream(), cudaStreamCaptureModeThreadLocal), "batch: capture");
-    if (rc != SEM_OK) return rc;
-    const VecArgs none{};
-    for (int k = 0; k < K && rc == SEM_OK; ++k) {
-        if (which == 0) {
-            rc = launch_bax<double, double, 0>(B, B->grid_ax64);
-            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate64>(B, none);
-        } else {
-            rc = which == 1 ? launch_bax<float, __nv_bfloat16, 2>(B, B->grid_ax32)
-                            : launch_bax<float, float, 2>(B, B->grid_ax32);
-            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate32>(B, none);
+    // current device state of the members (to keep it for continuing problems)
+    std::vector<BatchProb> old(B->probs.size());
+    if (!old.empty()) {
+        rc = cuda_check(cudaMemcpyAsync(old.data(), B->d_probs, sizeof(BatchProb) * old.size(),
+                                        cudaMemcpyDeviceToHost, stream()), "batch: state read");
+        if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
+        if (rc != SEM_OK) return rc;
+    }
+    std::vector<BatchProb> hp(n);
+    std::vector<BatchItem> ax, vec;
+    bool any_init = false;
+    for (int k = 0; k < n && rc == SEM_OK; ++k) {
+        Problem *P = probs[k];
+        if (B->mode != 0) rc = mixed_prepare(P, B->mode == 1 ? kGBF16 : kGF32);
+        if (rc != SEM_OK) break;
+        BatchProb &q = hp[k];
+        memset(&q, 0, sizeof q);
+        for (size_t j = 0; j < B->probs.size(); ++j)
+            if (B->probs[j] == P) q = old[j];       // keep the solve state
+        q.nq = P->nq; q.nx = P->nx; q.ny = P->ny; q.nz = P->nz;
+        q.E = P->E; q.nL = P->nL;
+        q.G = P->G; q.G16 = static_cast<const __nv_bfloat16 *>(P->G16); q.G32 = static_cast<const float *>(P->G32);
+        q.x = P->x; q.r = P->r; q.p = P->p; q.w = P->w;
+        q.d32 = P->d32; q.r32 = P->r32; q.p32 = P->p32; q.w32 = P->w32;
+        q.st = P->st; q.st_in = P->st_in ? P->st_in : P->st;
+        if (start[k]) {
+            q.b = b[k];
+            q.init = 1;
+            q.finished = 0;
+            q.refine = 0;
+            q.outer_done = 0;
+            any_init = true;
         }
+        const int epb = kBatchThreads / (P->nq * P->nq);
+        q.ax_first = int(ax.size());
+        for (int64_t e = 0; e < P->E; e += epb)
+            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(epb, P->E - e)), 0});
+        q.ax_count = int(ax.size()) - q.ax_first;
+        const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
+        q.vec_first = int(vec.size());
+        for (int64_t l = 0; l < P->nL; l += chunk)
+            vec.push_back(BatchItem{k, P->nq, l, int(std::min<int64_t>(chunk, P->nL - l)), 0});
+        q.vec_count = int(vec.size()) - q.vec_first;
     }
-    count_launches(-2 * int64_t(K));
-    const int rc_end = cuda_check(cudaStreamEndCapture(stream(), &g), "batch: end capture");
-    if (rc == SEM_OK) rc = rc_end;
-    if (rc == SEM_OK) rc = cuda_check(cudaGraphInstantiate(&B->graph[which], g, 0), "batch: instantiate");
-    if (g) cudaGraphDestroy(g);
+    if (rc != SEM_OK) return rc;
+    int cap_part = std::max(B->cap_ax, B->cap_vec);
+    rc = grow(&B->d_probs, &B->cap_probs, std::max(n, 1));
     if (rc == SEM_OK) {
-        B->graph_iters = K;
-        B->graph_stream = stream();
+        int cap_t = B->cap_probs, cap_f = B->cap_probs;
+        // tickets (2 per problem) and finished ids follow the problem capacity
+        if (B->tickets) dev_free(B->tickets);
+        if (B->finished_ids) dev_free(B->finished_ids);
+        B->tickets = static_cast<uint32_t *>(dev_alloc(sizeof(uint32_t) * 2 * size_t(cap_t)));
+        B->finished_ids = static_cast<int32_t *>(dev_alloc(sizeof(int32_t) * (size_t(cap_f) + 1)));
+        if (!B->tickets || !B->finished_ids) rc = SEM_ENOMEM;
+    }
+    if (rc == SEM_OK) rc = grow(&B->d_ax, &B->cap_ax, std::max<int>(int(ax.size()), 1));
+    if (rc == SEM_OK) rc = grow(&B->d_vec, &B->cap_vec, std::max<int>(int(vec.size()), 1));
+    if (rc == SEM_OK) rc = grow(&B->part, &cap_part, std::max(B->cap_ax, B->cap_vec));
+    if (rc != SEM_OK) return rc;
+    B->probs.assign(probs, probs + n);
+    B->n_ax = int(ax.size());
+    B->n_vec = int(vec.size());
+    B->any_init = any_init;
+    if (n)
+        rc = cuda_check(cudaMemcpyAsync(B->d_probs, hp.data(), sizeof(BatchProb) * n, cudaMemcpyHostToDevice,
+                                        stream()), "batch: descriptors");
+    if (rc == SEM_OK && !ax.empty())
+        rc = cuda_check(cudaMemcpyAsync(B->d_ax, ax.data(), sizeof(BatchItem) * ax.size(), cudaMemcpyHostToDevice,
+                                        stream()), "batch: items");
+    if (rc == SEM_OK && !vec.empty())
+        rc = cuda_check(cudaMemcpyAsync(B->d_vec, vec.data(), sizeof(BatchItem) * vec.size(), cudaMemcpyHostToDevice,
+                                        stream()), "batch: items");
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemsetAsync(B->tickets, 0, sizeof(uint32_t) * 2 * size_t(B->cap_probs), stream()), "batch");
+    // the finished list restarts with the new membership
+    if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(&B->ctl->n_finished, 0, sizeof(unsigned), stream()), "batch");
+    B->seen_finished = 0;
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
     }
     return rc;
 }
 
-// Replay the captured iterations until every problem's (inner) CG has
-// stopped or maxit iterations have run.
-static int run_until_done(Batch *B, int which, int maxit, unsigned target) {
-    const int64_t max_replays = (int64_t(maxit) + B->graph_iters - 1) / B->graph_iters;
-    for (int64_t rep = 0; rep < max_replays; ++rep) {
-        int rc = read_ctl(B);
-        if (rc != SEM_OK) return rc;
-        if (B->ctl_host->n_done >= target) return SEM_OK;
-        rc = cuda_check(cudaGraphLaunch(B->graph[which], stream()), "batch: graph launch");
-        if (rc != SEM_OK) return rc;
-        count_launches(2 * int64_t(B->graph_iters));
-    }
-    return read_ctl(B);
+void batch_destroy(Batch *B) {
+    if (!B) return;
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    void *ptrs[] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids, B->ctl};
+    for (void *q : ptrs)
+        if (q) dev_free(q);
+    if (B->ctl_host) cudaFreeHost(B->ctl_host);
+    delete B;
 }
 
-int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int maxit, int mode, double inner_tol,
-                int max_outer, int64_t *iters, double *res) {
-    if (mode < 0 || mode > 2) return set_error(SEM_EARG, "batch_solve: mode must be 0 (fp64), 1 (bf16), 2 (fp32)");
-    if (maxit < 1) return set_error(SEM_EARG, "batch_solve: maxit must be >= 1");
-    const int n = batch_size(B);
-    VecArgs A{b_all, x_all, tol, inner_tol, maxit};
-    int rc = cuda_check(cudaMemsetAsync(B->ctl, 0, sizeof(BatchCtl), stream()), "batch: reset");
-    if (rc == SEM_OK) rc = launch_bvec<kVecInit64>(B, A);
+int batch_size(const Batch *B) { return int(B->probs.size()); }
+int64_t batch_total_nodes(const Batch *B) {
+    int64_t t = 0;
+    for (const Problem *P : B->probs) t += P->nL;
+    return t;
+}
+
+// K iterations of (operator, update) for the batch's precision, captured once
+// per membership.
+static int capture(Batch *B) {
+    if (B->graph && B->graph_stream == stream()) return SEM_OK;
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    int rc = cuda_check(cudaStreamBeginCapture(stream(), cudaStreamCaptureModeThreadLocal), "batch: capture");
     if (rc != SEM_OK) return rc;
-    if (mode == 0) {
-        rc = capture(B, 0);
-        if (rc == SEM_OK) rc = run_until_done(B, 0, maxit, unsigned(n));
-    } else {
-        rc = capture(B, mode);
-        for (int outer = 0; outer < max_outer && rc == SEM_OK; ++outer) {
-            rc = read_ctl(B);
-            if (rc != SEM_OK || B->ctl_host->n_outer_done >= unsigned(n)) break;
-            // inner solves still to finish: the problems not yet converged
-            const unsigned need = unsigned(n) - B->ctl_host->n_outer_done;
-            rc = reset_done(B);
-            if (rc == SEM_OK) rc = launch_bvec<kVecInner>(B, A);
-            if (rc == SEM_OK) rc = run_until_done(B, mode, maxit, need);
-            if (rc == SEM_OK) rc = launch_bvec<kVecCorrect>(B, A);
-            if (rc == SEM_OK) rc = launch_bax<double, double, 1>(B, B->grid_ax64);
-            if (rc == SEM_OK) rc = launch_bvec<kVecResidual>(B, A);
+    for (int k = 0; k < B->K && rc == SEM_OK; ++k) {
+        if (B->mode == 0) {
+            rc = launch_bax<double, double, 0>(B, B->grid_ax64);
+            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate64>(B);
+        } else {
+            rc = B->mode == 1 ? launch_bax<float, __nv_bfloat16, 2>(B, B->grid_ax32)
+                              : launch_bax<float, float, 2>(B, B->grid_ax32);
+            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate32>(B);
         }
     }
-    if (rc == SEM_OK) rc = launch_bvec<kVecCopyOut>(B, A);
+    count_launches(-2 * int64_t(B->K));
+    const int rc_end = cuda_check(cudaStreamEndCapture(stream(), &g), "batch: end capture");
+    if (rc == SEM_OK) rc = rc_end;
+    if (rc == SEM_OK) rc = cuda_check(cudaGraphInstantiate(&B->graph, g, 0), "batch: instantiate");
+    if (g) cudaGraphDestroy(g);
+    if (rc == SEM_OK) B->graph_stream = stream();
+    return rc;
+}
+
+// One round: start joining problems, K CG iterations, refinement of problems
+// whose inner solve ended (mixed).  Appends the problems that finished during
+// the round (indices into the member list) to *done.
+int batch_round(Batch *B, std::vector<int> *done) {
+    if (B->probs.empty()) return SEM_OK;
+    int rc = SEM_OK;
+    if (B->any_init) {
+        rc = launch_bvec<kVecInit64>(B);
+        if (rc == SEM_OK && B->mode != 0) rc = launch_bvec<kVecInner>(B);
+        if (rc == SEM_OK) rc = launch_flags(B, kFlagClearInit);
+        B->any_init = false;
+        if (rc != SEM_OK) return rc;
+    }
+    rc = capture(B);
+    if (rc == SEM_OK) rc = cuda_check(cudaGraphLaunch(B->graph, stream()), "batch: graph launch");
     if (rc != SEM_OK) return rc;
-    // per-problem results
+    count_launches(2 * int64_t(B->K));
+    if (B->mode != 0) {
+        rc = launch_flags(B, kFlagMarkRefine);
+        if (rc == SEM_OK) rc = launch_bvec<kVecCorrect>(B);
+        if (rc == SEM_OK) rc = launch_bax<double, double, 1>(B, B->grid_ax64);
+        if (rc == SEM_OK) rc = launch_bvec<kVecResidual>(B);
+        if (rc == SEM_OK) rc = launch_bvec<kVecInner>(B);
+        if (rc == SEM_OK) rc = launch_flags(B, kFlagClearRefine);
+        if (rc != SEM_OK) return rc;
+    }
+    rc = read_ctl(B);
+    if (rc != SEM_OK) return rc;
+    const unsigned nf = B->ctl_host->n_finished;
+    if (nf > B->seen_finished) {
+        std::vector<int32_t> ids(nf - B->seen_finished);
+        rc = cuda_check(cudaMemcpyAsync(ids.data(), B->finished_ids + B->seen_finished, sizeof(int32_t) * ids.size(),
+                                        cudaMemcpyDeviceToHost, stream()), "batch: finished list");
+        if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
+        if (rc != SEM_OK) return rc;
+        for (int32_t k : ids) done->push_back(k);
+        B->seen_finished = nf;
+    }
+    return SEM_OK;
+}
+
+// Per-problem results after the problem finished: iterations (CG, or inner
+// iterations for mixed) and the relative residual (recursive for CG, true
+// for mixed).
+int batch_results(Batch *B, int64_t *iters, double *res) {
+    const int n = batch_size(B);
     std::vector<BatchProb> hp(n);
     std::vector<CgState> hs(n);
-    rc = cuda_check(cudaMemcpyAsync(hp.data(), B->d_probs, sizeof(BatchProb) * n, cudaMemcpyDeviceToHost, stream()),
-                    "batch: results");
+    int rc = cuda_check(cudaMemcpyAsync(hp.data(), B->d_probs, sizeof(BatchProb) * n, cudaMemcpyDeviceToHost,
+                                        stream()), "batch: results");
     for (int k = 0; k < n && rc == SEM_OK; ++k)
-        rc = cuda_check(cudaMemcpyAsync(&hs[k], mode == 0 ? B->probs[k]->st : B->probs[k]->st_in, sizeof(CgState),
-                                        cudaMemcpyDeviceToHost, stream()), "batch: results");
+        rc = cuda_check(cudaMemcpyAsync(&hs[k], B->probs[k]->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
+                        "batch: results");
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
     if (rc != SEM_OK) return rc;
     for (int k = 0; k < n; ++k) {
-        if (mode == 0) {
+        if (B->mode == 0) {
             iters[k] = hs[k].iter;
             res[k] = hs[k].rho0 > 0.0 ? std::sqrt(hs[k].rho / hs[k].rho0) : 0.0;
         } else {
@@ -689,6 +767,72 @@ int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int ma
             res[k] = hp[k].res;
         }
     }
+    return SEM_OK;
+}
+
+// Fixed batch: every problem starts now; rounds until all have finished.
+int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int maxit, int mode, double inner_tol,
+                int max_outer, int64_t *iters, double *res) {
+    if (mode < 0 || mode > 2) return set_error(SEM_EARG, "batch_solve: mode must be 0 (fp64), 1 (bf16), 2 (fp32)");
+    if (maxit < 1) return set_error(SEM_EARG, "batch_solve: maxit must be >= 1");
+    const int n = batch_size(B);
+    if (mode != B->mode && B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    B->mode = mode;
+    B->tol = tol;
+    B->maxit = maxit;
+    B->inner_tol = inner_tol;
+    B->max_outer = max_outer;
+    std::vector<Problem *> ps = B->probs;
+    std::vector<const double *> bs(n);
+    std::vector<uint8_t> start(n, 1);
+    int64_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        bs[k] = b_all + off;
+        off += ps[k]->nL;
+    }
+    int rc = batch_set(B, ps.data(), bs.data(), start.data(), n);
+    std::vector<int> done;
+    // enough rounds for every problem's iteration limits
+    const int64_t per_solve = mode == 0 ? int64_t(maxit) : int64_t(maxit + 1) * std::max(1, max_outer);
+    const int64_t max_rounds = per_solve / std::max(1, B->K) + max_outer + 4;
+    for (int64_t round = 0; round < max_rounds && rc == SEM_OK && int(done.size()) < n; ++round)
+        rc = batch_round(B, &done);
+    if (rc != SEM_OK) return rc;
+    off = 0;
+    for (int k = 0; k < n && rc == SEM_OK; ++k) {
+        rc = cuda_check(cudaMemcpyAsync(x_all + off, ps[k]->x, sizeof(double) * ps[k]->nL, cudaMemcpyDeviceToDevice,
+                                        stream()), "batch: copy x");
+        off += ps[k]->nL;
+    }
+    if (rc != SEM_OK) return rc;
+    return batch_results(B, iters, res);
+}
+
+int batch_create(Problem **probs, int n, Batch **out) {
+    *out = nullptr;
+    if (n < 1) return set_error(SEM_EARG, "batch: needs at least one problem");
+    Batch *B = batch_new(0, 1e-8, 100000, 1e-3, 50, 16);
+    int64_t tot = 0;
+    for (int k = 0; k < n; ++k) tot += probs[k]->nL;
+    B->K = tot < (int64_t(1) << 22) ? 32 : 16;
+    std::vector<const double *> bs(n, nullptr);
+    std::vector<uint8_t> start(n, 0);
+    // prepare both mixed precisions up front so later solves need no allocation
+    int rc = SEM_OK;
+    for (int k = 0; k < n && rc == SEM_OK; ++k) {
+        rc = mixed_prepare(probs[k], kGBF16);
+        if (rc == SEM_OK) rc = mixed_prepare(probs[k], kGF32);
+    }
+    if (rc == SEM_OK) rc = batch_set(B, probs, bs.data(), start.data(), n);
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
+    if (rc != SEM_OK) {
+        batch_destroy(B);
+        return rc;
+    }
+    *out = B;
     return SEM_OK;
 }
 

@@ -228,6 +228,33 @@ __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, 
     return acc;
 }
 
+// b = mask(QQ^T f) on the box (copies summed in ascending local index).
+template <int NQ>
+__global__ void assemble_box_kernel(const double *__restrict__ f, double *__restrict__ b, int nL, int nx, int ny,
+                                    int nz) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nL) return;
+    const BoxNode bn = box_node<NQ>(l, nx, ny, nz);
+    if (bn.masked) {
+        b[l] = 0.0;
+        return;
+    }
+    const int z0 = bn.sz < 0 ? bn.oz : 0, z1 = bn.sz > 0 ? bn.oz : 0;
+    const int y0 = bn.sy < 0 ? bn.oy : 0, y1 = bn.sy > 0 ? bn.oy : 0;
+    const int x0 = bn.sx < 0 ? bn.ox : 0, x1 = bn.sx > 0 ? bn.ox : 0;
+    double s = 0.0;
+    bool first = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cz = c >> 2, cy = (c >> 1) & 1, cx = c & 1;
+        if (!((cz == 0 || bn.sz) && (cy == 0 || bn.sy) && (cx == 0 || bn.sx))) continue;
+        const double v = f[l + (cz ? z1 : z0) + (cy ? y1 : y0) + (cx ? x1 : x0)];
+        s = first ? v : s + v;
+        first = false;
+    }
+    b[l] = s;
+}
+
 // One CG update step over all local nodes (grid-stride), with the <r, r>
 // reduction: per-thread partials in Acc, block and grid sums in FP64, and the
 // last block closes the iteration (beta, counter, stop flag).

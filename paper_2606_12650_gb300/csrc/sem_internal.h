@@ -8,6 +8,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "sem.h"
 
@@ -63,6 +64,7 @@ struct Problem {
     double *B = nullptr;           // [nL] mass weights W |J|
     double *c = nullptr;           // [nL] 1 / multiplicity
 
+    bool maps_ready = false;       // the four arrays below exist (built on first use)
     // direct-stiffness sum: global ids with >= 2 copies, copies ascending
     int32_t *sh_ptr = nullptr, *sh_idx = nullptr;
     int64_t n_sh = 0, n_sh_copies = 0;
@@ -111,6 +113,7 @@ int cuda_check(cudaError_t err, const char *what);
 // ---- setup (sem_setup.cu) --------------------------------------------------
 void gll_rule_and_derivative(int N, double *xi, double *w, double *D);   // D row-major (N+1)^2
 int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out);
+int problem_maps(Problem *P);                 // gs maps, mask list, weights c (lazy)
 void problem_destroy(Problem *P);
 int launch_nodes(const Problem *P, const double *verts_dev, double *X);
 int launch_rhs_sin(const Problem *P, const double *verts_dev_or_null, double *b);
@@ -144,12 +147,30 @@ int pcg_solve(Problem *P, const double *b, double *x, double tol, int maxit, dou
 
 // ---- batches (sem_batch.cu) -------------------------------------------------
 struct Batch;
+Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_outer, int K);
+int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *start, int n);
+int batch_round(Batch *B, std::vector<int> *done);
+int batch_results(Batch *B, int64_t *iters, double *res);
 int batch_create(Problem **probs, int n, Batch **out);
 void batch_destroy(Batch *B);
 int64_t batch_total_nodes(const Batch *B);
 int batch_size(const Batch *B);
 int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int maxit, int mode, double inner_tol,
                 int max_outer, int64_t *iters, double *res);
+
+// ---- serving (sem_serve.cu) -------------------------------------------------
+struct Server;
+int serve_open(int capacity, double budget_gb, int mode, double tol, double inner_tol, int K, int maxit,
+               Server **out);
+int serve_submit(Server *S, int nx, int ny, int nz, int N, const double *verts, const double *b, bool assemble,
+                 double arrival, int64_t *ticket);
+int64_t serve_drain(Server *S, int64_t *out, int64_t cap);
+int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_completed);
+int serve_result(Server *S, int64_t ticket, double *x_out, bool x_on_device, int64_t *state, int64_t *iters,
+                 double *rel_res, double *latency_ms);
+int64_t serve_nodes_of(const Server *S, int64_t ticket);
+double serve_now(const Server *S);
+void serve_close(Server *S);
 
 // ---- device facts (sem_probe.cu) --------------------------------------------
 int probe_fma_rate(int dtype, int iters, double *flops_per_s);   // dtype 0: f64, 1: f32

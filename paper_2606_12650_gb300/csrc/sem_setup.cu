@@ -367,8 +367,6 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         count_launches(1);
         rc = cuda_check(cudaGetLastError(), "geom_kernel");
     }
-    HostMaps M;
-    if (rc == SEM_OK) build_maps(nx, ny, nz, N, M);  // overlaps the geometry kernel
     if (rc == SEM_OK) {
         int32_t hbad = 0;
         rc = cuda_check(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, stream()), "mesh: flag");
@@ -380,15 +378,6 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         }
     }
     if (bad) dev_free(bad);
-    if (rc == SEM_OK) {
-        P->n_sh = int64_t(M.sh_ptr.size()) - 1;
-        P->n_sh_copies = int64_t(M.sh_idx.size());
-        P->n_mask = int64_t(M.msk_idx.size());
-        P->sh_ptr = upload(M.sh_ptr, &rc);
-        P->sh_idx = upload(M.sh_idx, &rc);
-        P->msk_idx = upload(M.msk_idx, &rc);
-        P->c = upload(M.c, &rc);
-    }
     if (rc == SEM_OK) {
         P->x = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->r = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
@@ -408,6 +397,26 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
     }
     *out = P;
     return SEM_OK;
+}
+
+// Sorted-segment gather-scatter maps, mask list and multiplicity weights,
+// built on the host on first use (the CG, batched and served hot paths use
+// the structured box copies instead and never need them).
+int problem_maps(Problem *P) {
+    if (P->maps_ready) return SEM_OK;
+    HostMaps M;
+    build_maps(P->nx, P->ny, P->nz, P->N, M);
+    int rc = SEM_OK;
+    P->n_sh = int64_t(M.sh_ptr.size()) - 1;
+    P->n_sh_copies = int64_t(M.sh_idx.size());
+    P->n_mask = int64_t(M.msk_idx.size());
+    P->sh_ptr = upload(M.sh_ptr, &rc);
+    P->sh_idx = upload(M.sh_idx, &rc);
+    P->msk_idx = upload(M.msk_idx, &rc);
+    P->c = upload(M.c, &rc);
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "maps: sync");
+    if (rc == SEM_OK) P->maps_ready = true;
+    return rc;
 }
 
 void problem_destroy(Problem *P) {

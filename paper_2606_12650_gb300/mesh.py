@@ -131,3 +131,55 @@ class Batch:
         if self.handle:
             sem.run("batch_free", self.handle)
             self.handle = 0
+
+
+class Server:
+    """Continuous-batching solve server (one sem.run call per method)."""
+
+    def __init__(self, capacity: int = 256, budget_gb: float = 40.0, mode: int = 1, tol: float = 1e-8,
+                 inner_tol: float = 1e-3, K: int = 8, maxit: int = 100000):
+        h = sem.OutInt()
+        sem.run("serve_open", int(capacity), float(budget_gb), int(mode), float(tol), float(inner_tol),
+                int(K), int(maxit), h)
+        self.handle = h.value
+
+    def now(self) -> float:
+        o = sem.OutDouble()
+        sem.run("serve_now", self.handle, o)
+        return o.value
+
+    def submit(self, nx, ny, nz, N, verts, b, arrival: float, assemble: bool = False) -> int:
+        """Queue a request; with assemble=True, b is a nodal source f and the
+        server solves with mask(QQ^T f)."""
+        t = sem.OutInt()
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        sem.run("serve_submit", self.handle, int(nx), int(ny), int(nz), int(N), sem.HostArray(v),
+                sem.HostArray(bb), int(bool(assemble)), float(arrival), t)
+        return t.value
+
+    def drain(self, cap: int = 4096):
+        """Tickets completed since the last drain."""
+        out = np.zeros(cap, dtype=np.int64)
+        n = sem.OutInt()
+        sem.run("serve_drain", self.handle, sem.HostArray(out), int(cap), n)
+        return out[: n.value].tolist()
+
+    def step(self):
+        """Returns (queued, active, completed)."""
+        q, a, c = sem.OutInt(), sem.OutInt(), sem.OutInt()
+        sem.run("serve_step", self.handle, q, a, c)
+        return q.value, a.value, c.value
+
+    def result(self, ticket: int, x=None):
+        """Returns (state, iters, rel_res, latency_ms); x (host numpy array or
+        CUDA tensor) receives the solution when state == 2."""
+        st, it, res, lat = sem.OutInt(), sem.OutInt(), sem.OutDouble(), sem.OutDouble()
+        xa = sem.HostArray(x) if isinstance(x, np.ndarray) else x
+        sem.run("serve_result", self.handle, int(ticket), xa, st, it, res, lat)
+        return st.value, it.value, res.value, lat.value
+
+    def close(self):
+        if self.handle:
+            sem.run("serve_close", self.handle)
+            self.handle = 0

@@ -1,0 +1,93 @@
+"""The solve server: continuous batching with HBM-budget admission.
+
+Each served result must reach the tolerance with the oracle's own operator
+(true residual within 1.5x of tol); a request served alone and inside a
+stream of other requests must give bit-identical solutions (its arithmetic
+never mixes with other requests'); a budget that fits one request at a time
+must serialise the requests and still serve them all.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_12650_gb300.inputs import box_vertices, normal_field
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _requests(count, seed, e_hi=96):
+    from paper_2606_12650_gb300.serve import make_requests
+    return make_requests(count, seed, e_lo=2, e_hi=e_hi, orders=(3, 5, 7))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_served_results_reach_tolerance(semlib, oracle_mod, mode):
+    from paper_2606_12650_gb300 import Server
+    from paper_2606_12650_gb300.serve import run_stream
+    reqs = _requests(14, seed=7)
+    arr = np.linspace(0.0, 0.05, len(reqs))          # overlapping arrivals
+    srv = Server(capacity=64, budget_gb=8.0, mode=mode, tol=1e-8, K=8)
+    out = run_stream(srv, reqs, arr, collect_x=True)
+    srv.close()
+    assert np.all(out["latency_ms"] > 0)
+    for k, r in enumerate(reqs):
+        P = oracle_mod.Problem(r["nx"], r["ny"], r["nz"], r["N"], r["verts"])
+        b = P.mask(P.gs(r["f"]))
+        if not np.any(b):
+            assert not np.any(out["x"][k])
+            continue
+        assert P.true_residual(b, out["x"][k]) <= 1.5e-8, k
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_alone_and_in_the_mix_are_identical(semlib, mode):
+    from paper_2606_12650_gb300 import Server
+    from paper_2606_12650_gb300.serve import run_stream
+    reqs = _requests(10, seed=11)
+    probe = 4
+    srv = Server(capacity=64, budget_gb=8.0, mode=mode, tol=1e-8, K=8)
+    mixed = run_stream(srv, reqs, np.linspace(0.0, 0.02, len(reqs)), collect_x=True)
+    srv.close()
+    srv = Server(capacity=64, budget_gb=8.0, mode=mode, tol=1e-8, K=8)
+    alone = run_stream(srv, [reqs[probe]], np.zeros(1), collect_x=True)
+    srv.close()
+    np.testing.assert_array_equal(alone["x"][0], mixed["x"][probe])
+    assert alone["iters"][0] == mixed["iters"][probe]
+
+
+def test_budget_admits_one_at_a_time(semlib):
+    from paper_2606_12650_gb300 import Server
+    reqs = _requests(5, seed=3, e_hi=64)
+    big = max(r["nL"] for r in reqs)
+    # room for the largest request but not for two of them
+    budget_gb = (big * (48 + 8 + 32 + 8 + 12 + 16) + (1 << 20)) * 1.5 / 1e9
+    srv = Server(capacity=64, budget_gb=budget_gb, mode=1, tol=1e-8, K=8)
+    t0 = srv.now()
+    for r in reqs:
+        srv.submit(r["nx"], r["ny"], r["nz"], r["N"], r["verts"], r["f"], t0, assemble=True)
+    done = []
+    for _ in range(100000):
+        q, a, c = srv.step()
+        assert a <= 1
+        done += srv.drain()
+        if c == len(reqs):
+            break
+    assert len(done) == len(reqs)
+    srv.close()
+
+
+def test_server_errors(semlib):
+    from paper_2606_12650_gb300 import Server, sem
+    with pytest.raises(sem.SemError) as e:
+        Server(capacity=0)
+    assert e.value.code == sem.SEM_EARG
+    srv = Server(capacity=4, budget_gb=0.001, mode=1)
+    verts = box_vertices(8, 8, 8, 0.05, seed=1)
+    with pytest.raises(sem.SemError) as e:   # larger than the whole budget
+        srv.submit(8, 8, 8, 7, verts, np.zeros(512 * 512), 0.0)
+    assert e.value.code == sem.SEM_ENOMEM
+    with pytest.raises(sem.SemError) as e:
+        srv.result(12345)
+    assert e.value.code == sem.SEM_EHANDLE
+    srv.close()
