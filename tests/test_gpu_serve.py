@@ -57,23 +57,27 @@ def test_alone_and_in_the_mix_are_identical(semlib, mode):
 
 
 def test_budget_admits_one_at_a_time(semlib):
+    """Equal-size requests and a budget for 1.5 of them: one active at a time."""
     from paper_2606_12650_gb300 import Server
-    reqs = _requests(5, seed=3, e_hi=64)
-    big = max(r["nL"] for r in reqs)
-    # room for the largest request but not for two of them
-    budget_gb = (big * (48 + 8 + 32 + 8 + 12 + 16) + (1 << 20)) * 1.5 / 1e9
+    nx, ny, nz, N = 3, 3, 2, 5
+    nL = nx * ny * nz * (N + 1) ** 3
+    budget_gb = (nL * (48 + 8 + 32 + 8 + 12 + 16) + (1 << 20)) * 1.5 / 1e9
     srv = Server(capacity=64, budget_gb=budget_gb, mode=1, tol=1e-8, K=8)
     t0 = srv.now()
-    for r in reqs:
-        srv.submit(r["nx"], r["ny"], r["nz"], r["N"], r["verts"], r["f"], t0, assemble=True)
+    for k in range(5):
+        srv.submit(nx, ny, nz, N, box_vertices(nx, ny, nz, 0.05, seed=k), normal_field(nL, 50 + k), t0,
+                   assemble=True)
     done = []
     for _ in range(100000):
         q, a, c = srv.step()
         assert a <= 1
         done += srv.drain()
-        if c == len(reqs):
+        if c == 5:
             break
-    assert len(done) == len(reqs)
+    assert len(done) == 5
+    for tk in done:
+        st, it, res, lat = srv.result(tk)
+        assert st == 2 and res <= 1e-8 and it > 0
     srv.close()
 
 
