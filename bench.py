@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--inner-tol", type=float, default=1e-3, help="inner FP32 CG residual reduction")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pcg", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200, help="requests per arrival rate")
+    ap.add_argument("--serve-rates", default="100,200,500,1000,2000,5000")
     ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
@@ -314,6 +317,17 @@ def run_ours(a):
     if not a.no_batched:
         batched = run_batched(a, world, rank, barrier, stream, sem, torch, dist)
 
+    # ---- served: Poisson arrivals, continuous batching, HBM-budget admission
+    served = None
+    if not a.no_serve and rank == 0:
+        from paper_2606_12650_gb300.serve import sweep
+        rates = [float(r) for r in a.serve_rates.split(",")]
+        rows = sweep(rates, a.serve_requests, seed=5, mode=1, budget_gb=40.0, K=8, tol=a.tol)
+        served = {"workload": f"Poisson arrivals, {a.serve_requests} requests per rate, E log-uniform [8, 8192] "
+                              f"(near-cubic boxes), N in {{5,7}}, jitter 5%, random source, tol {a.tol:g}, "
+                              "mixed precision (BF16 G), 40 GB admission budget, 8 CG iterations per round",
+                  "rates": rows}
+
     # ---- end to end through the public API, host buffers
     e2e = None
     if not a.no_e2e:
@@ -365,7 +379,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "pcg": pcg, "mixed": mixed, "batched": batched,
+                "pcg": pcg, "mixed": mixed, "batched": batched, "serve": served,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
