@@ -152,7 +152,8 @@ class ClockSampler:
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+    from paper_2606_12650_gb300.ranks import rank_env
+    return rank_env()
 
 
 # ------------------------------------------------------------------ oracle (CPU) timing
@@ -200,6 +201,7 @@ def run_ours(a):
     __graft_entry__.build()
     from paper_2606_12650_gb300 import Mesh, sem
     from paper_2606_12650_gb300.inputs import box_vertices, normal_field
+    from paper_2606_12650_gb300.ranks import Job, rank_seed
 
     rank, local, world = dist_env()
     torch.cuda.set_device(local)
@@ -208,15 +210,13 @@ def run_ours(a):
     sem.init([f"--device={local}"])
     stream = sem.stream()
     torch.cuda.set_stream(stream)
-
-    def barrier():
-        if world > 1:
-            dist.barrier(device_ids=[local])
+    job = Job(world, dist, device=torch.device("cuda", local), local=local)
+    barrier = job.barrier
 
     nx, N = a.nx, a.N
     E = nx ** 3
     M = Mesh(nx, nx, nx, N, box_vertices(nx, nx, nx, 0.05, seed=2))
-    f = torch.from_numpy(normal_field(M.nL, 3 + rank)).cuda()
+    f = torch.from_numpy(normal_field(M.nL, rank_seed(3, rank))).cuda()
     b = f.clone()
     M.gs(b)
     M.mask(b)
@@ -240,16 +240,7 @@ def run_ours(a):
         torch.cuda.synchronize()
     barrier()
     launches = sem.launch_count() - n_launch0
-    t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    dofs = float(E * N ** 3 * iters_total)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-        dofs = float(dd.item())
+    t_max, dofs = job.aggregate(ev0.elapsed_time(ev1), float(E * N ** 3 * iters_total))
     value = dofs / (t_max * 1e-3) / 1e9
     true_res = M.true_res(b, x)
 
@@ -310,12 +301,12 @@ def run_ours(a):
     # ---- mixed precision: FP32 inner CG (BF16 geometric factors), FP64 refinement
     mixed = None
     if not a.no_mixed:
-        mixed = run_mixed(a, M, b, x, t_max, world, barrier, stream, sem, torch, dist)
+        mixed = run_mixed(a, M, b, x, t_max, job, stream, sem, torch)
 
     # ---- batched: many uneven problems, one persistent launch per CG phase
     batched = None
     if not a.no_batched:
-        batched = run_batched(a, world, rank, barrier, stream, sem, torch, dist)
+        batched = run_batched(a, job, rank, stream, sem, torch)
 
     # ---- served: Poisson arrivals, continuous batching, HBM-budget admission
     served = None
@@ -352,14 +343,7 @@ def run_ours(a):
             e_iters += it
         t_e2e = time.perf_counter() - t0
         barrier()
-        e_dofs = float(E * N ** 3 * e_iters)
-        if world > 1:
-            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
-            dd = torch.tensor([e_dofs], device="cuda", dtype=torch.float64)
-            dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-            e_dofs = float(dd.item())
+        t_e2e, e_dofs = job.aggregate(t_e2e, float(E * N ** 3 * e_iters))
         e2e = {"value": e_dofs / t_e2e / 1e9, "unit": "GDOF/s", "h2d_bytes_per_step": M.nL * 8,
                "d2h_bytes_per_step": M.nL * 8, "ms_per_step": 1e3 * t_e2e / a.steps}
         assert np.allclose(xh.numpy(), x.cpu().numpy(), rtol=0, atol=0)
@@ -399,10 +383,11 @@ def hbm_peak():
         return 6800.0, "fallback (6.8 TB/s)"
 
 
-def run_mixed(a, M, b, x64, t64_ms, world, barrier, stream, sem, torch, dist):
+def run_mixed(a, M, b, x64, t64_ms, job, stream, sem, torch):
     """Same problem and tolerance through mixed-precision refinement; also a
     1e-10 solve (FP64 CG and mixed) for the error table."""
     E, N = a.nx ** 3, a.N
+    world, barrier = job.world, job.barrier
     xm = torch.empty_like(b)
     for _ in range(a.warmup):
         M.cg_mixed(b, xm, a.tol, 50, a.inner_tol, a.maxit, 1)
@@ -417,15 +402,7 @@ def run_mixed(a, M, b, x64, t64_ms, world, barrier, stream, sem, torch, dist):
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    t_ms = ev0.elapsed_time(ev1)
-    dofs = float(E * N ** 3 * inner_tot)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
-        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-        dofs = float(dd.item())
+    t_ms, dofs = job.aggregate(ev0.elapsed_time(ev1), float(E * N ** 3 * inner_tot))
     err_vs_fp64 = float((xm - x64).abs().max().item() / x64.abs().max().item())
     true_res = M.true_res(b, xm)
     # inner operator kernel (FP32, BF16 G), timed alone on libsem's stream
@@ -468,7 +445,7 @@ def run_mixed(a, M, b, x64, t64_ms, world, barrier, stream, sem, torch, dist):
                           "mixed_rel_res_true": res10, "err_vs_fp64_cg_inf": err10}}
 
 
-def run_batched(a, world, rank, barrier, stream, sem, torch, dist):
+def run_batched(a, job, rank, stream, sem, torch):
     """256 independent problems (E log-uniform in [8, 4096] as near-cubic boxes,
     N uniform in {3, 5, 7, 9}, jitter 5 %, random right-hand sides), each CG
     phase of all of them one persistent launch: FP64 CG and mixed refinement
@@ -476,7 +453,9 @@ def run_batched(a, world, rank, barrier, stream, sem, torch, dist):
     import numpy as np
     from paper_2606_12650_gb300 import Batch, Mesh
     from paper_2606_12650_gb300.inputs import batch_specs, box_vertices, normal_field
-    specs = batch_specs(a.batch_count, seed=4 + 1000 * rank, e_lo=8, e_hi=4096, orders=(3, 5, 7, 9))
+    from paper_2606_12650_gb300.ranks import rank_seed
+    world, barrier = job.world, job.barrier
+    specs = batch_specs(a.batch_count, seed=rank_seed(4, rank), e_lo=8, e_hi=4096, orders=(3, 5, 7, 9))
     t0 = time.perf_counter()
     meshes, bs = [], []
     for s in specs:
@@ -506,15 +485,7 @@ def run_batched(a, world, rank, barrier, stream, sem, torch, dist):
         its, res = B.solve(b_all, x_all, a.tol, a.maxit, mode, a.inner_tol)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        dofs = float((gdof_per_iter * its).sum())
-        if world > 1:
-            tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms = float(tt.item())
-            dd = torch.tensor([dofs], device="cuda", dtype=torch.float64)
-            dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-            dofs = float(dd.item())
+        ms, dofs = job.aggregate(e0.elapsed_time(e1), float((gdof_per_iter * its).sum()))
         out[name] = {"ms": ms, "gdofs": dofs / (ms * 1e-3) / 1e9, "solves_per_s": 1e3 * len(meshes) * world / ms,
                      "iters_total": int(its.sum()), "iters_max": int(its.max()), "max_rel_res": float(res.max())}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed_bf16"]["ms"]
