@@ -46,7 +46,19 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
-              for f in ("sem_ax_kernel.cuh", "sem_ax.cu", "sem_device.cuh", "sem_internal.h")]
+              for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
+                        "sem_internal.h")]
+VARIANTS = {0: "columns", 1: "lines", 2: "persistent"}
+
+
+def kernel_label(variant, epb, N, t, gt):
+    """Name of the CG-operator kernel the tuner chose."""
+    q = N + 1
+    if variant == 1:
+        return f"ax_lines_kernel<{q},{t},{gt},CG> ({epb} elements/block)"
+    if variant == 2:
+        return f"ax32p_kernel<{q},{gt},CG> (persistent)"
+    return f"ax_kernel<{q},{t},{gt},CG> (columns)"
 
 
 def parse():
@@ -71,6 +83,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200, help="requests per arrival rate")
     ap.add_argument("--serve-rates", default="100,200,500,1000,2000,5000")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-tune", action="store_true", help="keep the built-in operator table")
+    ap.add_argument("--tune-reps", type=int, default=10, help="timed launches per tuner candidate")
     return ap.parse_args()
 
 
@@ -222,6 +236,17 @@ def run_ours(a):
     M.mask(b)
     x = torch.empty_like(b)
 
+    # ---- per-order operator tuner: every variant of the FP64 operator and of
+    # the mixed path's FP32 (BF16 G) operator timed on this problem, fastest kept
+    tune = None
+    if not a.no_tune:
+        tune = {"N": N, "reps": a.tune_reps}
+        for kind, name in ((sem.TUNE_F64, "fp64"), (sem.TUNE_F32_G16, "fp32_bf16")):
+            cands = M.autotune(kind, reps=a.tune_reps)
+            v, e, us = sem.autotune_get(kind, N)
+            tune[name] = {"chosen": {"variant": VARIANTS[v], "epb": e, "us": us},
+                          "candidates": [{"variant": VARIANTS[c[0]], "epb": c[1], "us": c[2]} for c in cands]}
+
     for _ in range(a.warmup):
         iters, rel = M.cg_solve(b, x, a.tol, a.maxit)
 
@@ -267,9 +292,13 @@ def run_ours(a):
             traffic = t.get("bytes_per_launch")
     except (OSError, ValueError):
         pass
+    v64, e64, _ = sem.autotune_get(sem.TUNE_F64, N)
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "kernel": f"ax_kernel<{N + 1},2,double,double,CG>", "launch_ms": ax_ms,
+                "kernel": kernel_label(v64, e64, N, "double", "double"), "launch_ms": ax_ms,
+                "flops_note": "achieved counts the operator's direct-evaluation flops, 12(N+1)^4 + 15(N+1)^3 per "
+                              "element; the line kernel's even-odd split executes fewer (48 instead of 64 "
+                              "operations per 1d line at N = 7)",
                 "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
                 "hbm_gbs_at_alg_bytes": bytes_alg / (ax_ms * 1e-3) / 1e9,
                 "fp64_probe_gflops": fp64.value / 1e9,
@@ -363,7 +392,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "pcg": pcg, "mixed": mixed, "batched": batched, "serve": served,
+                "pcg": pcg, "mixed": mixed, "batched": batched, "serve": served, "autotune": tune,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
@@ -438,7 +467,8 @@ def run_mixed(a, M, b, x64, t64_ms, job, stream, sem, torch):
             "inner_iters_per_solve": inner_tot // max(a.steps, 1), "outer_iters": outer,
             "rel_res_true": true_res, "err_vs_fp64_cg_inf": err_vs_fp64,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "traffic": None, "kernel": f"ax_kernel<{N + 1},4,float,bf16,CG>",
+                         "traffic": None,
+                         "kernel": kernel_label(*sem.autotune_get(sem.TUNE_F32_G16, N)[:2], N, "float", "bf16"),
                          "launch_ms": ax_ms, "alg_bytes_per_launch": alg, "peak_source": how},
             "tol_1e-10": {"fp64_cg_iters": it10, "fp64_ms": 1e3 * t_fp64_10,
                           "mixed_inner_iters": in10, "mixed_outer_iters": out10, "mixed_ms": 1e3 * t_mix_10,

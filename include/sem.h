@@ -86,6 +86,9 @@ typedef void (*sem_free_fn)(void *ptr, void *ctx);
  *   --device=K        CUDA device ordinal (default 0)
  *   --verbose=V       0 silent (default), 1 setup messages on stderr
  *   --hbm-budget=GB   cap on device bytes the library allocates (default: none)
+ *   --autotune-table=PATH  operator table written by "autotune_save"; a file
+ *                     that cannot be read or has a bad entry fails sem_init
+ *                     with SEM_EARG (the table starts from built-in defaults)
  * Unknown arguments are ignored.  A second sem_init without sem_finalize
  * returns SEM_EINIT.  Queries the device (name, SM count, shared memory per
  * block, the analogue of the paper's "context" table, Section V-B). */
@@ -171,6 +174,29 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   "peak_fma"  dtype (0 f64, 1 f32), iters, OUT flops_per_s
  *               measured FMA issue rate of the FP64 or FP32 pipe (device fact
  *               for the ALU roofline; not part of the method)
+ *   Operator tuner.  The local operator exists in several variants, all
+ *   computing the same map: 0 "columns" (one thread per (i, j) column of an
+ *   element, FP64), 1 "lines" (whole r, s and t lines per thread with the
+ *   even-odd split of D; elements per block epb chosen at launch), 2
+ *   "persistent" (TMA-pipelined columns, FP32 only).  The variant in use is
+ *   kept per kind (0 FP64, 1 FP32 with FP32 G, 2 FP32 with BF16 G) and per N;
+ *   the paper's runtime specialises kernels on N and its scripts pick the
+ *   thread layout (Section VIII-B); here the choice is made by timing.
+ *   Changing it makes every captured CG graph be captured again.
+ *   "autotune"  handle, kind, reps, cand (HOST double[3 cap] or NONE), cap,
+ *               OUT n_cand
+ *               Runs each candidate of `kind` at the problem's N as the CG
+ *               operator (reps timed launches after 2 warm-ups, on the
+ *               problem's own CG vectors, which it overwrites) and keeps the
+ *               fastest.  cand receives (variant, epb, microseconds per
+ *               launch) per candidate, n_cand their number (<= 16).
+ *   "autotune_get" kind, N, OUT variant, OUT epb, OUT us
+ *   "autotune_set" kind, N, variant, epb      SEM_EARG if the variant does
+ *               not exist for the kind or epb does not fit a block
+ *   "autotune_save" path (HOST NUL-terminated)  writes the table as text:
+ *               lines "kind N variant epb us", '#' comments
+ *   "autotune_load" path (HOST NUL-terminated)  reads such a file (all
+ *               entries checked before any is used; SEM_EARG on a bad line)
  *   "batch"     n, handles (HOST int64[n]), OUT batch
  *               Group n problems (made with "mesh", any sizes and orders) for
  *               batched solves.  Their local vectors are concatenated in the

@@ -458,6 +458,63 @@ int run_cg_ax32(ArgReader &R) {
     return rc != SEM_OK ? rc : launch_ax32_cg(P, int(gprec));
 }
 
+// autotune(handle, kind, reps, cand HOST double[3 cap] | NONE, cap, OUT n_cand)
+int run_autotune(ArgReader &R) {
+    if (!R.need(6)) return R.err;
+    Problem *P = get_problem(R, 0, false);
+    const int64_t kind = R.i(1, "kind"), reps = R.i(2, "reps"), cap = R.i(4, "cap");
+    if (R.err) return R.err;
+    if (cap < 0 || cap > 64) return R.fail(SEM_EARG, "cap must be in [0, 64]");
+    double *cand = static_cast<double *>(R.host(3, size_t(cap) * 3 * sizeof(double), "cand", true));
+    int64_t *n_out = static_cast<int64_t *>(R.out(5, SEM_ARG_OUT_INT, "n_cand"));
+    if (R.err) return R.err;
+    int n = 0;
+    TuneChoice best{};
+    const int rc = tune_problem(P, int(kind), int(reps), cand, int(cap), &n, &best);
+    if (rc == SEM_OK) *n_out = n;
+    return rc;
+}
+
+// autotune_get(kind, N, OUT variant, OUT epb, OUT us)
+int run_autotune_get(ArgReader &R) {
+    if (!R.need(5)) return R.err;
+    const int64_t kind = R.i(0, "kind"), N = R.i(1, "N");
+    int64_t *ov = static_cast<int64_t *>(R.out(2, SEM_ARG_OUT_INT, "variant"));
+    int64_t *oe = static_cast<int64_t *>(R.out(3, SEM_ARG_OUT_INT, "epb"));
+    double *ou = static_cast<double *>(R.out(4, SEM_ARG_OUT_DOUBLE, "us"));
+    if (R.err) return R.err;
+    if (kind < 0 || kind >= kTuneKinds) return R.fail(SEM_EARG, "kind must be 0, 1 or 2");
+    if (N < 1 || N > kMaxQ - 1) return R.fail(SEM_EARG, "N must be in [1, 9]");
+    const TuneChoice c = tune_get(int(kind), int(N) + 1);
+    *ov = c.variant;
+    *oe = c.epb;
+    *ou = c.us;
+    return SEM_OK;
+}
+
+// autotune_set(kind, N, variant, epb)
+int run_autotune_set(ArgReader &R) {
+    if (!R.need(4)) return R.err;
+    const int64_t kind = R.i(0, "kind"), N = R.i(1, "N"), variant = R.i(2, "variant"), epb = R.i(3, "epb");
+    if (R.err) return R.err;
+    const TuneChoice c{int(variant), int(epb), 0.0};
+    const int rc = tune_check(int(kind), int(N) + 1, c);
+    if (rc != SEM_OK) return rc;
+    sync_stream("autotune_set");
+    tune_set(int(kind), int(N) + 1, c);
+    return SEM_OK;
+}
+
+// autotune_save(path HOST) / autotune_load(path HOST): NUL-terminated path
+int run_autotune_file(ArgReader &R, bool save) {
+    if (!R.need(1)) return R.err;
+    const char *path = static_cast<const char *>(R.host(0, 1, "path"));
+    if (R.err) return R.err;
+    if (save) return tune_save(path);
+    sync_stream("autotune_load");
+    return tune_load(path);
+}
+
 int run_cg_mixed(ArgReader &R) {
     if (!R.need(11)) return R.err;
     Problem *P = get_problem(R, 0);
@@ -791,12 +848,19 @@ int sem_init(int argc, const char **argv) {
     if (g.up) return set_error(SEM_EINIT, "sem_init: already initialised");
     int device = 0, verbose = 0;
     double budget_gb = 0.0;
+    const char *table = nullptr;
     for (int a = 0; a < argc; ++a) {
         if (!argv || !argv[a]) continue;
         const char *s = argv[a];
         if (!strncmp(s, "--device=", 9)) device = atoi(s + 9);
         else if (!strncmp(s, "--verbose=", 10)) verbose = atoi(s + 10);
         else if (!strncmp(s, "--hbm-budget=", 13)) budget_gb = atof(s + 13);
+        else if (!strncmp(s, "--autotune-table=", 17)) table = s + 17;
+    }
+    tune_reset();
+    if (table) {
+        const int trc = tune_load(table);
+        if (trc != SEM_OK) return trc;
     }
     int rc = cuda_check(cudaSetDevice(device), "sem_init: cudaSetDevice");
     if (rc != SEM_OK) return rc;
@@ -923,6 +987,11 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "serve_drain") rc = run_serve_drain(R);
     else if (k == "serve_close") rc = run_serve_close(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
+    else if (k == "autotune") rc = run_autotune(R);
+    else if (k == "autotune_get") rc = run_autotune_get(R);
+    else if (k == "autotune_set") rc = run_autotune_set(R);
+    else if (k == "autotune_save") rc = run_autotune_file(R, true);
+    else if (k == "autotune_load") rc = run_autotune_file(R, false);
     else return set_error(SEM_EKERNEL, "sem_run: unknown kernel '" + k + "'");
     return rc;
 }

@@ -1,6 +1,8 @@
-// sem_ax.cu -- FP64 instantiations of the local Poisson operator (the
-// kernel itself is in sem_ax_kernel.cuh): plain y = A_local x, and the CG
-// variant with the fused p-update and <p, A p> reduction.
+// sem_ax.cu -- FP64 local Poisson operator: the column kernel's
+// instantiations (sem_ax_kernel.cuh) -- plain y = A_local x, the CG variant
+// with the fused p-update and <p, A p> reduction, the Jacobi-PCG variant --
+// and the dispatch to the variant the per-order tuner chose (the line kernel
+// lives in sem_ax_lines64.cu).
 #include "sem_ax_kernel.cuh"
 
 namespace sem {
@@ -8,6 +10,8 @@ namespace sem {
 int prepare_ax(const Problem *Pb) { return prepare_ax_any<double, double>(Pb); }
 
 int launch_ax(const Problem *Pb, const double *x, double *y) {
+    const TuneChoice c = tune_get(kTuneF64, Pb->nq);
+    if (c.variant == kAxLines) return launch_lines64(Pb, x, y, 0, c.epb);
     AxArgs<double, double> a = ax_args<double, double>(Pb, Pb->G, Pb->partials, Pb->st);
     a.x = x;
     a.y = y;
@@ -15,6 +19,8 @@ int launch_ax(const Problem *Pb, const double *x, double *y) {
 }
 
 int launch_ax_cg(const Problem *Pb) {
+    const TuneChoice c = tune_get(kTuneF64, Pb->nq);
+    if (c.variant == kAxLines) return launch_lines64(Pb, nullptr, nullptr, 1, c.epb);
     AxArgs<double, double> a = ax_args<double, double>(Pb, Pb->G, Pb->partials, Pb->st);
     a.x = Pb->r;
     a.y = Pb->w;
@@ -23,6 +29,8 @@ int launch_ax_cg(const Problem *Pb) {
 }
 
 int launch_ax_pcg(const Problem *Pb) {
+    const TuneChoice c = tune_get(kTuneF64, Pb->nq);
+    if (c.variant == kAxLines) return launch_lines64(Pb, nullptr, nullptr, 2, c.epb);
     AxArgs<double, double> a = ax_args<double, double>(Pb, Pb->G, Pb->partials, Pb->st);
     a.x = Pb->r;
     a.y = Pb->w;

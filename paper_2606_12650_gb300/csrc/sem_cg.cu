@@ -168,6 +168,7 @@ static int graph_iters_for(const Problem *P) {
 }
 
 static int capture_graph(Problem *P) {
+    if (P->graph_epoch != tune_epoch()) problem_drop_graphs(P);   // operator variant changed
     if (P->graph) return SEM_OK;
     const int K = graph_iters_for(P);
     cudaGraph_t g = nullptr;

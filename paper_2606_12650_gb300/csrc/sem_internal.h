@@ -83,6 +83,8 @@ struct Problem {
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;
 
+    uint64_t graph_epoch = 0;      // operator-variant epoch the graphs above were captured at
+
     // mixed precision (allocated on first use): geometric factors rounded to
     // FP32 or BF16 ([nL][6]), FP32 inner-CG vectors and the inner CG state
     void *G32 = nullptr;           // float
@@ -97,6 +99,39 @@ struct Problem {
 
 // storage precision of the geometric factors in mixed-precision inner solves
 enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
+
+// ---- operator variants and the per-order tuner (sem_tune.cu) ---------------
+// Variants of the local operator: the column kernel of sem_ax_kernel.cuh
+// (one thread per (i, j) column, fixed elements per block), the line kernel
+// of sem_ax_lines.cuh (whole lines per thread, even-odd split, elements per
+// block chosen at launch), and the persistent TMA-pipelined column kernel of
+// sem_ax32p.cuh (FP32 only).
+enum AxVariant : int { kAxColumns = 0, kAxLines = 1, kAxPersistent = 2, kAxVariants = 3 };
+// What is tuned: the FP64 operator, and the FP32 operator with FP32 or BF16
+// geometric factors.
+enum TuneKind : int { kTuneF64 = 0, kTuneF32G32 = 1, kTuneF32G16 = 2, kTuneKinds = 3 };
+struct TuneChoice {
+    int variant;
+    int epb;       // elements per block (line kernel); 0 = the variant's own
+    double us;     // measured time of one CG-operator launch (0: not measured)
+};
+TuneChoice tune_get(int kind, int nq);
+void tune_set(int kind, int nq, const TuneChoice &c);     // bumps the epoch
+uint64_t tune_epoch();                                    // graphs captured earlier are stale
+void tune_reset();                                        // back to the built-in defaults
+int tune_check(int kind, int nq, const TuneChoice &c);    // SEM_OK or SEM_EARG (error set)
+int tune_kind_of_gprec(int gprec);
+// Times every candidate of `kind` on P's CG operator (reps launches each),
+// keeps the fastest.  cand: up to cap (variant, epb, us) triples.
+int tune_problem(Problem *P, int kind, int reps, double *cand, int cap, int *n_cand, TuneChoice *best);
+int tune_save(const char *path);
+int tune_load(const char *path);
+// line-kernel launchers (sem_ax_lines64.cu, sem_ax_lines32.cu); mode 0: y = A x,
+// 1: CG operator on P's vectors, 2: Jacobi-PCG operator
+int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb);
+int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb);
+bool lines_epb_ok(int nq, int epb, size_t elem_bytes);
+void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 
 // ---- runtime services (sem_api.cu) ---------------------------------------
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)

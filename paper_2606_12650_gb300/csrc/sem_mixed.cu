@@ -109,6 +109,7 @@ void mixed_release(Problem *P) {
 static int graph32_iters_for(const Problem *P) { return P->nL < (1 << 20) ? 64 : 32; }
 
 static int capture_inner(Problem *P, int gprec) {
+    if (P->graph_epoch != tune_epoch()) problem_drop_graphs(P);   // operator variant changed
     if (P->graph32[gprec] && P->graph32_stream == stream()) return SEM_OK;
     for (auto &g : P->graph32)
         if (g) {

@@ -165,6 +165,7 @@ static int launch_pcg_update(const Problem *P) {
 }
 
 static int capture_pcg(Problem *P) {
+    if (P->graph_epoch != tune_epoch()) problem_drop_graphs(P);   // operator variant changed
     if (P->graph_pcg && P->graph_stream == stream()) return SEM_OK;
     if (P->graph_pcg) {
         cudaGraphExecDestroy(P->graph_pcg);

@@ -419,6 +419,18 @@ int problem_maps(Problem *P) {
     return rc;
 }
 
+// Drops the captured CG graphs (they hold the operator variant chosen at
+// capture time); the next solve captures them again.
+void problem_drop_graphs(Problem *P) {
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    if (P->graph_pcg) cudaGraphExecDestroy(P->graph_pcg);
+    for (auto &g : P->graph32)
+        if (g) cudaGraphExecDestroy(g);
+    P->graph = P->graph_pcg = nullptr;
+    P->graph32[0] = P->graph32[1] = nullptr;
+    P->graph_epoch = tune_epoch();
+}
+
 void problem_destroy(Problem *P) {
     if (!P) return;
     if (P->graph) cudaGraphExecDestroy(P->graph);

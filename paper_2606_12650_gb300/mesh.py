@@ -92,6 +92,10 @@ class Mesh:
     def jacobi(self, dinv):
         sem.run("jacobi", self.handle, dinv)
 
+    def autotune(self, kind: int, reps: int = 10):
+        """Tune the operator variant for this problem's order (sem.autotune)."""
+        return sem.autotune(self.handle, kind, reps)
+
     def true_res(self, b, x) -> float:
         o = sem.OutDouble()
         sem.run("true_res", self.handle, b, x, o)

@@ -293,3 +293,44 @@ def dot_noalloc(c, u, v, n: int, out, stream_handle: int | None = None) -> None:
 def stream():
     """The torch.cuda.Stream libsem runs on (when ``init`` created one)."""
     return _keep.get("stream")
+
+
+# ---------------------------------------------------------------- operator tuner
+TUNE_F64, TUNE_F32_G32, TUNE_F32_G16 = 0, 1, 2           # what is tuned
+VARIANT_COLUMNS, VARIANT_LINES, VARIANT_PERSISTENT = 0, 1, 2
+VARIANT_NAMES = {VARIANT_COLUMNS: "columns", VARIANT_LINES: "lines", VARIANT_PERSISTENT: "persistent"}
+
+
+def autotune(handle: int, kind: int, reps: int = 10):
+    """Time every operator variant of `kind` on problem `handle` (its order)
+    and keep the fastest.  Returns [(variant, elements_per_block, us), ...]."""
+    import numpy as np
+    cand = np.zeros(3 * 32, dtype=np.float64)
+    n = OutInt()
+    run("autotune", int(handle), int(kind), int(reps), HostArray(cand), 32, n)
+    return [(int(cand[3 * c]), int(cand[3 * c + 1]), float(cand[3 * c + 2])) for c in range(n.value)]
+
+
+def autotune_get(kind: int, N: int):
+    """The variant in use for (kind, N): (variant, elements_per_block, us)."""
+    v, e, u = OutInt(), OutInt(), OutDouble()
+    run("autotune_get", int(kind), int(N), v, e, u)
+    return v.value, e.value, u.value
+
+
+def autotune_set(kind: int, N: int, variant: int, epb: int = 0) -> None:
+    run("autotune_set", int(kind), int(N), int(variant), int(epb))
+
+
+def _path_arg(path: str):
+    import numpy as np
+    b = np.frombuffer(str(path).encode() + b"\0", dtype=np.uint8).copy()
+    return HostArray(b)
+
+
+def autotune_save(path: str) -> None:
+    run("autotune_save", _path_arg(path))
+
+
+def autotune_load(path: str) -> None:
+    run("autotune_load", _path_arg(path))

@@ -76,3 +76,39 @@ def test_product_path_fails_loudly_without_library(tmp_path):
     from paper_2606_12650_gb300 import sem
     with pytest.raises(RuntimeError, match="libsem.so not found"):
         sem._open(str(tmp_path / "missing.so"))
+
+
+def test_autotune_table_is_checked_at_init(lib, tmp_path):
+    """--autotune-table: every entry is validated before the device is
+    touched (kind, N in [1, 9], variant available for the kind, elements per
+    block fitting one block); a bad file fails sem_init with SEM_EARG."""
+    from paper_2606_12650_gb300 import sem
+
+    def init(*args):
+        arr = (ctypes.c_char_p * len(args))(*[a.encode() for a in args])
+        return lib.sem_init(len(args), arr)
+
+    assert init(f"--autotune-table={tmp_path / 'missing.txt'}") == sem.SEM_EARG
+    assert "cannot read" in sem.last_error()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("# comment\n0 7 1 2 10.0\n0 7 9 1\n")
+    assert init(f"--autotune-table={bad}") == sem.SEM_EARG
+    assert "line 3" in sem.last_error()
+    for entry in ("1 7 0 0",      # column kernel is FP64 only
+                  "0 7 2 0",      # persistent kernel is FP32 only
+                  "0 10 1 1",     # N above 9
+                  "0 0 1 1",      # N below 1
+                  "0 7 1 600",    # 600 elements of 64 threads do not fit a block
+                  "0 7 1 0",      # line kernel needs elements per block
+                  "3 7 1 1",      # no such kind
+                  "0 7"):         # too few fields
+        f = tmp_path / "one.txt"
+        f.write_text(entry + "\n")
+        assert init(f"--autotune-table={f}") == sem.SEM_EARG, entry
+    good = tmp_path / "good.txt"
+    good.write_text("# kind N variant epb us\n0 7 1 2 1800.5\n2 7 1 4\n1 3 2 0\n\n")
+    rc = init(f"--autotune-table={good}")
+    if rc == sem.SEM_OK:          # a GPU is present
+        assert lib.sem_finalize() == sem.SEM_OK
+    else:                         # the table passed; the device query failed
+        assert rc == sem.SEM_ECUDA, sem.last_error()
