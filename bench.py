@@ -48,14 +48,15 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
               for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
                         "sem_internal.h")]
-VARIANTS = {0: "columns", 1: "lines", 2: "persistent"}
+VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch"}
 
 
 def kernel_label(variant, epb, N, t, gt):
     """Name of the CG-operator kernel the tuner chose."""
     q = N + 1
-    if variant == 1:
-        return f"ax_lines_kernel<{q},{t},{gt},CG> ({epb} elements/block)"
+    if variant in (1, 3):
+        pf = ", G prefetched" if variant == 3 else ""
+        return f"ax_lines_kernel<{q},{t},{gt},CG> ({epb} elements/block{pf})"
     if variant == 2:
         return f"ax32p_kernel<{q},{gt},CG> (persistent)"
     return f"ax_kernel<{q},{t},{gt},CG> (columns)"

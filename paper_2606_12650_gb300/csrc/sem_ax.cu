@@ -25,6 +25,7 @@ int launch_ax_cg(const Problem *Pb) {
     a.x = Pb->r;
     a.y = Pb->w;
     a.p = Pb->p;
+    a.xs = Pb->x;   // x += alpha p of the previous iteration
     return launch_ax_any<double, double, true>(Pb, a);
 }
 
@@ -35,6 +36,7 @@ int launch_ax_pcg(const Problem *Pb) {
     a.x = Pb->r;
     a.y = Pb->w;
     a.p = Pb->p;
+    a.xs = Pb->x;   // x += alpha p of the previous iteration
     a.dinv = Pb->dinv;
     return launch_ax_any<double, double, true, true>(Pb, a);
 }

@@ -48,6 +48,8 @@ struct AxArgs {
     CgState *st;
     int32_t *status;
     const T *dinv;      // PCG: Jacobi inverse diagonal
+    T *xs;              // CG: solution, updated x += alpha p_old before p is replaced
+                        // (the previous iteration's x update, deferred); nullptr: none
     int64_t E;
     T D[kMaxQ * kMaxQ];
 };
@@ -96,7 +98,8 @@ struct AxShape {
 template <int NQ, int EPB, typename T, typename GT, bool CG, typename DSrc, bool PRE = false>
 __device__ __forceinline__ bool ax_group(const T *x, T *y, T *p, const GT *G, const DSrc &D, T beta,
                                          int64_t e0, int ne, T *regA, uint64_t *bar, uint32_t phase,
-                                         int32_t *status, T *part, const T *dinv = nullptr) {
+                                         int32_t *status, T *part, const T *dinv = nullptr, T *xs = nullptr,
+                                         T xalpha = T(0)) {
     using S = AxShape<NQ, EPB, T>;
     constexpr int NQ2 = S::NQ2, NP = S::NP;
     T *regB = regA + S::SLAB;
@@ -140,6 +143,7 @@ __device__ __forceinline__ bool ax_group(const T *x, T *y, T *p, const GT *G, co
                 const int q = eb * NP + k * NQ2 + ij;
                 // PCG: p = M^-1 r + beta p with the Jacobi M
                 const T zq = PRE ? dinv[nb + k * NQ2 + ij] * s1[q] : s1[q];
+                if (xs) xs[nb + k * NQ2 + ij] = fma(xalpha, s2[q], xs[nb + k * NQ2 + ij]);
                 const T pn = fma(beta, s2[q], zq);
                 s2[q] = pn;
                 xk[k] = pn;
@@ -227,10 +231,11 @@ ax_kernel(const AxArgs<T, GT> P) {
     const int64_t e0 = int64_t(blockIdx.x) * EPB;
     const int ne = int(min(int64_t(EPB), P.E - e0));
     const T beta = CG ? T(P.st->beta) : T(0);
+    const T xalpha = CG ? T(P.st->alpha) : T(0);   // read before this launch's last block replaces it
     T part = T(0);
     const ParamD<T, GT> D{P};
     if (!ax_group<NQ, EPB, T, GT, CG, ParamD<T, GT>, PRE>(P.x, P.y, P.p, P.G, D, beta, e0, ne, regA, bar, 0u,
-                                                         P.status, &part, P.dinv))
+                                                         P.status, &part, P.dinv, CG ? P.xs : nullptr, xalpha))
         return;
     if (CG) {
         // the column's partial is formed in T; the block and grid sums are FP64

@@ -80,33 +80,75 @@ __device__ __forceinline__ void eo_apply(const T (&u)[NQ], T (&y)[NQ], const EoM
     }
 }
 
-struct LineShape {
-    // values per buffer for epb elements: + 2 x 16 B slack for the slab
-    // alignment shift, rounded to 16 B
-    template <typename T>
-    static __host__ __device__ int slab(int np, int epb) {
-        const int vpq = 16 / int(sizeof(T));
-        return (epb * np + 2 * vpq + vpq - 1) / vpq * vpq;
+// In-register rotation v[m] <- v[(m - R) mod NQ] for a per-thread R
+// (NQ a power of two): log2(NQ) stages of selects, no local memory.
+template <int NQ, typename T>
+__device__ __forceinline__ void rotate_right(T (&v)[NQ], int R) {
+#pragma unroll
+    for (int bit = 1; bit < NQ; bit <<= 1) {
+        const bool on = (R & bit) != 0;
+        T w[NQ];
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) w[m] = on ? v[(m - bit) & (NQ - 1)] : v[m];
+#pragma unroll
+        for (int m = 0; m < NQ; ++m) v[m] = w[m];
     }
-    template <typename T>
-    static __host__ __device__ size_t smem(int np, int epb) {
-        return 16 + 3 * size_t(slab<T>(np, epb)) * sizeof(T);
+}
+
+// Shared-memory layout.  The staged input slab(s) keep the global layout
+// (TMA copies them as they are).  U and V, written and read only by this
+// kernel, are padded for N+1 = 8: node (i, j, k) of an element at
+// k P2 + j P1 + i with P1 = 9, P2 = 72, so the rows and the columns a warp
+// touches at one step fall in distinct banks (FP32; two lanes per bank pair
+// in FP64, the minimum for 8-byte values) -- unpadded, rows 32 B apart put
+// 8 lanes on one bank.  Other orders keep the compact layout (measured:
+// padding there costs more in occupancy than it saves in conflicts).
+template <int NQ>
+struct LinePad {
+    static constexpr int P1 = NQ == 8 ? NQ + 1 : NQ, P2 = NQ * P1, NPP = NQ * P2;
+};
+
+struct LineShape {
+    // values per buffer for epb elements: the larger of the staged slab
+    // (+ 2 x 16 B slack for its alignment shift) and the padded U / V
+    // layout, rounded to 16 B
+    static __host__ __device__ int region(int nq, int epb, int elem_bytes) {
+        const int vpq = 16 / elem_bytes;
+        const int slab = epb * nq * nq * nq + 2 * vpq;
+        const int pad = epb * nq * nq * (nq == 8 ? nq + 1 : nq);
+        const int m = slab > pad ? slab : pad;
+        return (m + vpq - 1) / vpq * vpq;
+    }
+    static __host__ __device__ size_t smem(int nq, int epb, int elem_bytes) {
+        return 16 + 3 * size_t(region(nq, epb, elem_bytes)) * size_t(elem_bytes);
     }
 };
 
-template <int NQ, typename T, typename GT, bool CG, bool PRE>
+// PF (BF16 factors only): the element's geometric factors are loaded into
+// registers (3 words per node) before the slab wait, so their latency
+// overlaps the TMA copy instead of stalling phase 2.
+template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF = false>
 __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P) {
+    static_assert(!PF || sizeof(GT) == 2, "G prefetch is for BF16 factors");
     constexpr int NQ2 = NQ * NQ, NP = NQ2 * NQ;
+    constexpr int P1 = LinePad<NQ>::P1, P2 = LinePad<NQ>::P2, NPP = LinePad<NQ>::NPP;
+    // N+1 = 8: the staged slab's rows and columns are read in a per-thread
+    // rotated order (then rotated back in registers), so a warp's lanes hit
+    // distinct banks: rows of 8 values start 32 B (FP32) or 64 B (FP64)
+    // apart, 4 or 2 to a 128-byte bank row, hence the rotation by row / 4
+    // or row / 2; columns of one warp differ in k, hence the rotation by k.
+    constexpr bool ROT = NQ == 8;
+    constexpr int RPB = sizeof(T) == 8 ? 2 : 4;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     const AxArgs<T, GT> &A = P.a;
     if (CG && A.st->done) return;  // solve finished: the rest of the graph is a no-op
 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    const int SL = LineShape::slab<T>(NP, P.epb);
+    const int RG = LineShape::region(NQ, P.epb, int(sizeof(T)));
     T *regA = reinterpret_cast<T *>(smem + 16);
-    T *regB = regA + SL;
-    T *regC = regB + SL;
+    T *regB = regA + RG;
+    T *regC = regB + RG;
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
     const int64_t e0 = int64_t(blockIdx.x) * P.epb;
@@ -132,29 +174,45 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     }
     slab_edges(s1, src1, pl1, tid, nthreads);
     if (CG) slab_edges(s2, src2, pl2, tid, nthreads);
-    const bool ok = mbar_wait_bounded(bar, 0u, A.status);
-    if (__syncthreads_or(!ok)) {
-        mbar_wait_bounded(bar, 0u, nullptr);  // let copies in flight land before leaving
-        return;
-    }
 
     const int eb = tid / NQ2;
     const int ab = tid - eb * NQ2;
     const int a = ab % NQ, b = ab / NQ;
     const bool act = eb < ne;
     const int64_t nb = (e0 + eb) * NP;
-    const int rq = b * NQ2 + a * NQ;   // r line (j, k) = (a, b): first node
-    const int cq = b * NQ2 + a;        // s line (i, k) = (a, b): first node, stride NQ
-    const int tq = b * NQ + a;         // t line (i, j) = (a, b): first node, stride NQ2
+    unsigned gw[PF ? NQ : 1][3];
+    if (PF && act) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) {
+            const unsigned *gq = reinterpret_cast<const unsigned *>(A.G + 6 * (nb + k * NQ2 + b * NQ + a));
+            gw[k][0] = __ldg(gq);
+            gw[k][1] = __ldg(gq + 1);
+            gw[k][2] = __ldg(gq + 2);
+        }
+    }
+    const bool ok = mbar_wait_bounded(bar, 0u, A.status);
+    if (__syncthreads_or(!ok)) {
+        mbar_wait_bounded(bar, 0u, nullptr);  // let copies in flight land before leaving
+        return;
+    }
+
+    const int rq = b * NQ2 + a * NQ;   // r line (j, k) = (a, b) of the slab: first node
+    const int cq = b * NQ2 + a;        // s line (i, k) = (a, b) of the slab: first node, stride NQ
+    const int tq = b * NQ + a;         // t line (i, j) = (a, b) of the slab: first node, stride NQ2
+    const int rp = b * P2 + a * P1;    // the same lines in the padded U / V layout
+    const int cp = b * P2 + a;
+    const int tp = b * P1 + a;
 
     T xk[NQ];
     if (CG) {
         const T beta = T(A.st->beta);
+        const T xalpha = T(A.st->alpha);   // read before this launch's last block replaces it
         if (act) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const int q = eb * NP + k * NQ2 + tq;
                 const T zq = PRE ? A.dinv[nb + k * NQ2 + tq] * s1[q] : s1[q];
+                if (A.xs) A.xs[nb + k * NQ2 + tq] = fma(xalpha, s2[q], A.xs[nb + k * NQ2 + tq]);
                 const T pn = fma(beta, s2[q], zq);
                 s2[q] = pn;
                 xk[k] = pn;
@@ -167,23 +225,37 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
         for (int k = 0; k < NQ; ++k) xk[k] = s1[eb * NP + k * NQ2 + tq];
     }
     const T *SX = (CG ? s2 : s1) + eb * NP;
-    T *SU = (CG ? regA : regB) + eb * NP;
-    T *SV = regC + eb * NP;
+    T *SU = (CG ? regA : regB) + eb * NPP;
+    T *SV = regC + eb * NPP;
 
     // ---- (1) gradient lines
     T ut[NQ];
     if (act) {
         T u[NQ], y[NQ];
+        if (ROT) {
+            const int R = (ab / RPB) & (NQ - 1);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SX[rq + l];
+            for (int l = 0; l < NQ; ++l) u[l] = SX[rq + ((l + R) & (NQ - 1))];
+            rotate_right<NQ, T>(u, R);
+        } else {
+#pragma unroll
+            for (int l = 0; l < NQ; ++l) u[l] = SX[rq + l];
+        }
         eo_apply<NQ, T>(u, y, P.d);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rq + l] = y[l];
+        for (int l = 0; l < NQ; ++l) SU[rp + l] = y[l];
+        if (ROT) {
+            const int R = b & (NQ - 1);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SX[cq + l * NQ];
+            for (int l = 0; l < NQ; ++l) u[l] = SX[cq + ((l + R) & (NQ - 1)) * NQ];
+            rotate_right<NQ, T>(u, R);
+        } else {
+#pragma unroll
+            for (int l = 0; l < NQ; ++l) u[l] = SX[cq + l * NQ];
+        }
         eo_apply<NQ, T>(u, y, P.d);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cq + l * NQ] = y[l];
+        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = y[l];
         eo_apply<NQ, T>(xk, ut, P.d);
     }
     __syncthreads();
@@ -193,12 +265,18 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     if (act) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            const int q = k * NQ2 + tq;
-            const T ur = SU[q], us = SV[q];
+            const int pq = k * P2 + tp;
+            const T ur = SU[pq], us = SV[pq];
             T g[6];
-            load_g6(A.G, nb + q, g);
-            SU[q] = g[0] * ur + g[1] * us + g[2] * ut[k];
-            SV[q] = g[1] * ur + g[3] * us + g[4] * ut[k];
+            if constexpr (PF) {
+                const float2 g01 = bf16x2_to_float2(gw[k][0]), g23 = bf16x2_to_float2(gw[k][1]),
+                             g45 = bf16x2_to_float2(gw[k][2]);
+                g[0] = g01.x; g[1] = g01.y; g[2] = g23.x; g[3] = g23.y; g[4] = g45.x; g[5] = g45.y;
+            } else {
+                load_g6(A.G, nb + k * NQ2 + tq, g);
+            }
+            SU[pq] = g[0] * ur + g[1] * us + g[2] * ut[k];
+            SV[pq] = g[1] * ur + g[3] * us + g[4] * ut[k];
             wt[k] = g[2] * ur + g[4] * us + g[5] * ut[k];
         }
     }
@@ -209,15 +287,15 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     if (act) {
         T u[NQ], y[NQ];
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SU[rq + l];
+        for (int l = 0; l < NQ; ++l) u[l] = SU[rp + l];
         eo_apply<NQ, T>(u, y, P.dt);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rq + l] = y[l];
+        for (int l = 0; l < NQ; ++l) SU[rp + l] = y[l];
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SV[cq + l * NQ];
+        for (int l = 0; l < NQ; ++l) u[l] = SV[cp + l * P1];
         eo_apply<NQ, T>(u, y, P.dt);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cq + l * NQ] = y[l];
+        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = y[l];
         eo_apply<NQ, T>(wt, yt, P.dt);
     }
     __syncthreads();
@@ -227,10 +305,10 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     if (act) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            const int q = k * NQ2 + tq;
-            const T yv = (SU[q] + SV[q]) + yt[k];
-            A.y[nb + q] = yv;
-            if (CG) acc = fma(SX[q], yv, acc);
+            const int pq = k * P2 + tp;
+            const T yv = (SU[pq] + SV[pq]) + yt[k];
+            A.y[nb + k * NQ2 + tq] = yv;
+            if (CG) acc = fma(SX[k * NQ2 + tq], yv, acc);
         }
     }
     if (CG) {
@@ -283,14 +361,13 @@ inline int line_threads(int nq, int epb) {
     return t <= 512 ? t : 0;
 }
 
-template <int NQ, typename T, typename GT, bool CG, bool PRE>
+template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF>
 static int launch_lines_nq(const Problem *Pb, const AxLineArgs<T, GT> &L) {
-    constexpr int NP = NQ * NQ * NQ;
     const int nt = line_threads(NQ, L.epb);
     if (L.epb < 1 || nt == 0) return set_error(SEM_EARG, "ax lines: elements per block out of range");
-    const size_t sm = LineShape::smem<T>(NP, L.epb);
+    const size_t sm = LineShape::smem(NQ, L.epb, int(sizeof(T)));
     if (sm > size_t(227) * 1024) return set_error(SEM_EARG, "ax lines: shared memory per block too large");
-    auto kern = ax_lines_kernel<NQ, T, GT, CG, PRE>;
+    auto kern = ax_lines_kernel<NQ, T, GT, CG, PRE, PF>;
     // raise the dynamic shared-memory limit when a larger block is first
     // asked for (the tuner and the first solve do so before any capture)
     static size_t sm_set = 0;
@@ -307,18 +384,18 @@ static int launch_lines_nq(const Problem *Pb, const AxLineArgs<T, GT> &L) {
     return cuda_check(cudaGetLastError(), "ax_lines_kernel");
 }
 
-template <typename T, typename GT, bool CG, bool PRE = false>
+template <typename T, typename GT, bool CG, bool PRE = false, bool PF = false>
 static int launch_lines_any(const Problem *Pb, const AxLineArgs<T, GT> &L) {
     switch (Pb->nq) {
-        case 2: return launch_lines_nq<2, T, GT, CG, PRE>(Pb, L);
-        case 3: return launch_lines_nq<3, T, GT, CG, PRE>(Pb, L);
-        case 4: return launch_lines_nq<4, T, GT, CG, PRE>(Pb, L);
-        case 5: return launch_lines_nq<5, T, GT, CG, PRE>(Pb, L);
-        case 6: return launch_lines_nq<6, T, GT, CG, PRE>(Pb, L);
-        case 7: return launch_lines_nq<7, T, GT, CG, PRE>(Pb, L);
-        case 8: return launch_lines_nq<8, T, GT, CG, PRE>(Pb, L);
-        case 9: return launch_lines_nq<9, T, GT, CG, PRE>(Pb, L);
-        case 10: return launch_lines_nq<10, T, GT, CG, PRE>(Pb, L);
+        case 2: return launch_lines_nq<2, T, GT, CG, PRE, PF>(Pb, L);
+        case 3: return launch_lines_nq<3, T, GT, CG, PRE, PF>(Pb, L);
+        case 4: return launch_lines_nq<4, T, GT, CG, PRE, PF>(Pb, L);
+        case 5: return launch_lines_nq<5, T, GT, CG, PRE, PF>(Pb, L);
+        case 6: return launch_lines_nq<6, T, GT, CG, PRE, PF>(Pb, L);
+        case 7: return launch_lines_nq<7, T, GT, CG, PRE, PF>(Pb, L);
+        case 8: return launch_lines_nq<8, T, GT, CG, PRE, PF>(Pb, L);
+        case 9: return launch_lines_nq<9, T, GT, CG, PRE, PF>(Pb, L);
+        case 10: return launch_lines_nq<10, T, GT, CG, PRE, PF>(Pb, L);
         default: return set_error(SEM_EARG, "ax lines: unsupported order");
     }
 }

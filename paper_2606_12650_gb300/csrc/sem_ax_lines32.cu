@@ -7,7 +7,7 @@
 
 namespace sem {
 
-int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb) {
+int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb, bool pf) {
     if (!lines_epb_ok(P->nq, epb, sizeof(float))) return set_error(SEM_EARG, "ax lines: bad elements per block");
     if (gprec == kGF32) {
         AxArgs<float, float> a = ax_args<float, float>(P, static_cast<const float *>(P->G32), P->partials, P->st_in);
@@ -27,10 +27,12 @@ int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool c
         a.x = P->r32;
         a.y = P->w32;
         a.p = P->p32;
+        if (pf) return launch_lines_any<float, __nv_bfloat16, true, false, true>(P, line_args(a, P->oc.D, P->nq, epb));
         return launch_lines_any<float, __nv_bfloat16, true>(P, line_args(a, P->oc.D, P->nq, epb));
     }
     a.x = x;
     a.y = y;
+    if (pf) return launch_lines_any<float, __nv_bfloat16, false, false, true>(P, line_args(a, P->oc.D, P->nq, epb));
     return launch_lines_any<float, __nv_bfloat16, false>(P, line_args(a, P->oc.D, P->nq, epb));
 }
 

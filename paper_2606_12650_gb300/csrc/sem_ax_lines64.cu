@@ -8,10 +8,7 @@ namespace sem {
 
 bool lines_epb_ok(int nq, int epb, size_t elem_bytes) {
     if (nq < 2 || nq > kMaxQ || epb < 1 || line_threads(nq, epb) == 0) return false;
-    const int np = nq * nq * nq;
-    const int vpq = 16 / int(elem_bytes);
-    const size_t slab = size_t((epb * np + 2 * vpq + vpq - 1) / vpq * vpq);
-    return 16 + 3 * slab * elem_bytes <= size_t(200) * 1024;
+    return LineShape::smem(nq, epb, int(elem_bytes)) <= size_t(200) * 1024;
 }
 
 int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb) {
@@ -25,6 +22,7 @@ int launch_lines64(const Problem *P, const double *x, double *y, int mode, int e
     a.x = P->r;
     a.y = P->w;
     a.p = P->p;
+    a.xs = P->x;   // x += alpha p of the previous iteration
     if (mode == 1) return launch_lines_any<double, double, true>(P, line_args(a, P->oc.D, P->nq, epb));
     a.dinv = P->dinv;
     return launch_lines_any<double, double, true, true>(P, line_args(a, P->oc.D, P->nq, epb));

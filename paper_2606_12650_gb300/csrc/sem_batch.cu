@@ -319,7 +319,7 @@ __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, int64_t 
         const T alpha = T(st->alpha);
         T a = T(0);
         for (int v = tid; v < count / V; v += blockDim.x)
-            a += update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, P.nx, P.ny, P.nz, alpha);
+            update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, P.nx, P.ny, P.nz, alpha, a);
         acc = double(a);
     } else if (MODE == kVecInit64) {
         // <b, b> over global nodes (each counted at its first copy)

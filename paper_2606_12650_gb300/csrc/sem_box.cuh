@@ -51,50 +51,6 @@ __device__ __forceinline__ BoxNode box_node(int l, int nx, int ny, int nz) {
 
 }  // namespace sem
 
-namespace sem {
-
-// Fused direct-stiffness sum + CG update for one local node l.  The node's
-// copies are the combinations of {own, neighbour} element along each
-// direction in which it lies on an interior element face; enumerating
-// (t, s, r) choices with the lower element first lists them in ascending
-// local index.  All candidate loads are issued straight-line (predicated), so
-// they are independent; the sum then runs left to right over the valid ones,
-// which gives every copy of the node the same bits.  The node then updates
-// itself: x += alpha p, r -= alpha (QQ^T w).  Masked nodes are left as they
-// are (zero).  Returns the node's contribution to <r, r> (at its first copy).
-template <int NQ, typename T, typename Acc>
-__device__ __forceinline__ Acc update_node(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                          const T *__restrict__ w, int l, int nx, int ny, int nz, T alpha) {
-    const BoxNode b = box_node<NQ>(l, nx, ny, nz);
-    if (b.masked) return Acc(0);
-    // per direction: offset of option 0 (the lower element) and option 1
-    const int z0 = b.sz < 0 ? b.oz : 0, z1 = b.sz > 0 ? b.oz : 0;
-    const int y0 = b.sy < 0 ? b.oy : 0, y1 = b.sy > 0 ? b.oy : 0;
-    const int x0 = b.sx < 0 ? b.ox : 0, x1 = b.sx > 0 ? b.ox : 0;
-    T v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int cz = c >> 2, cy = (c >> 1) & 1, cx = c & 1;
-        const bool valid = (cz == 0 || b.sz) && (cy == 0 || b.sy) && (cx == 0 || b.sx);
-        const int off = (cz ? z1 : z0) + (cy ? y1 : y0) + (cx ? x1 : x0);
-        v[c] = valid ? __ldg(w + l + off) : T(0);
-    }
-    Acc s = Acc(v[0]);
-#pragma unroll
-    for (int c = 1; c < 8; ++c) {
-        const int cz = c >> 2, cy = (c >> 1) & 1, cx = c & 1;
-        const bool valid = (cz == 0 || b.sz) && (cy == 0 || b.sy) && (cx == 0 || b.sx);
-        if (valid) s = s + Acc(v[c]);
-    }
-    const T xn = fma(alpha, p[l], x[l]);
-    const T rn = fma(-alpha, T(s), r[l]);
-    x[l] = xn;
-    r[l] = rn;
-    return b.owner ? Acc(rn) * Acc(rn) : Acc(0);
-}
-
-}  // namespace sem
-
 #include "sem_device.cuh"
 
 namespace sem {
@@ -140,14 +96,24 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
     *reinterpret_cast<typename VecT<T, V>::type *>(p) = q;
 }
 
-// Fused gs + update for the V consecutive nodes l0 .. l0+V-1 (one row piece).
-// Same sums as update_node: for each (t, s) choice in ascending element
-// order, the r-face neighbour (node i = 0 only, lower element) comes before
-// the own value and the other r-face neighbour (node i = N only) after it.
-template <int NQ, int V, typename T, typename Acc, bool PRE = false>
-__device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                         const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha,
-                                         const T *__restrict__ dinv = nullptr, Acc *acc_rr = nullptr) {
+// Fused direct-stiffness sum + CG update for the V consecutive nodes
+// l0 .. l0+V-1 (one row piece of one element).  A node's copies are the
+// combinations of {own, neighbour} element along each direction in which it
+// lies on an interior element face; enumerating the (t, s) choices with the
+// lower element first, and within each the r-face neighbour of node 0 (lower
+// element) before the own value and that of node N (upper element) after it,
+// lists the copies in ascending local index -- the order of the sorted-
+// segment gather-scatter, so every copy of a node gets the same bits.  The
+// nodes then update themselves: r -= alpha (QQ^T w), and x += alpha p unless
+// DX (the x update is deferred to the next operator kernel, which holds p in
+// shared memory anyway).  Masked nodes are left as they are (zero).  <r, r>
+// (PRE: <r, M^-1 r> and <r, r> into *acc_rr) is accumulated into acc at each
+// node's first copy.
+template <int NQ, int V, typename T, typename Acc, bool PRE = false, bool DX = false>
+__device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                                          const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha,
+                                          Acc &acc, const T *__restrict__ dinv = nullptr,
+                                          Acc *acc_rr = nullptr) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
     const unsigned e = unsigned(l0) / unsigned(NP);
     const int q = l0 - int(e) * NP;
@@ -159,59 +125,89 @@ __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, 
     const int sy = j == 0 ? -1 : (j == N ? 1 : 0);
     const int sz = k == 0 ? -1 : (k == N ? 1 : 0);
     if ((sy < 0 && ey == 0) || (sy > 0 && ey == ny - 1) || (sz < 0 && ez == 0) || (sz > 0 && ez == nz - 1))
-        return Acc(0);                                    // on the cube boundary
+        return;                                           // on the cube boundary
     const int oy = sy * (nx * NP - N * NQ);
     const int oz = sz * (nx * ny * NP - N * NQ2);
     const bool has_lo = i0 == 0 && ex > 0;                // node i = 0 has a lower r neighbour
     const bool has_hi = i0 + V - 1 == N && ex < nx - 1;   // node i = N has a higher r neighbour
     const bool mask_lo = i0 == 0 && ex == 0;
     const bool mask_hi = i0 + V - 1 == N && ex == nx - 1;
-    const int z0 = sz < 0 ? oz : 0, z1 = sz > 0 ? oz : 0;
-    const int y0 = sy < 0 ? oy : 0, y1 = sy > 0 ? oy : 0;
-    T wv[4][V], lo[4], hi[4];
+    T sv[V];
+    if (sy == 0 && sz == 0) {
+        // Row inside the element in s and t: copies only across the r faces.
+        // Rows are handed out so that a warp holds rows of one class, so this
+        // branch is taken or skipped by whole warps.
+        T wv[V];
+        vload_nc<T, V>(w + l0, wv);
+        const T lo = has_lo ? __ldg(w + l0 - (NP - N)) : T(0);
+        const T hi = has_hi ? __ldg(w + l0 + (V - 1) + (NP - N)) : T(0);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int cz = c >> 1, cy = c & 1;
-        const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
-        const int off = l0 + (cz ? z1 : z0) + (cy ? y1 : y0);
-        if (valid) {
-            vload_nc<T, V>(w + off, wv[c]);
-            lo[c] = has_lo ? __ldg(w + off - (NP - N)) : T(0);              // element ex-1, node i = N
-            hi[c] = has_hi ? __ldg(w + off + (V - 1) + (NP - N)) : T(0);   // element ex+1, node i = 0
+        for (int v = 0; v < V; ++v) sv[v] = wv[v];
+        if (V < NQ) {
+            // no piece holds both node 0 and node N: one addition serves
+            // either (lo + own_0) or (own_N + hi)
+            const T a = has_lo ? lo : wv[V - 1];
+            const T b = has_lo ? wv[0] : hi;
+            const T sum = a + b;
+            if (has_lo) sv[0] = sum;
+            if (has_hi) sv[V - 1] = sum;
         } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) wv[c][v] = T(0);
-            lo[c] = hi[c] = T(0);
+            if (has_lo) sv[0] = lo + wv[0];
+            if (has_hi) sv[V - 1] = sv[V - 1] + hi;
         }
-    }
-    T xv[V], pv[V], rv[V];
-    vload<T, V>(x + l0, xv);
-    vload<T, V>(p + l0, pv);
-    vload<T, V>(r + l0, rv);
-    Acc acc = Acc(0), rr = Acc(0);
-    T dv[V];
-    if (PRE) vload<T, V>(dinv + l0, dv);
-    const bool owner_row = sy >= 0 && sz >= 0;
+    } else {
+        const int z0 = sz < 0 ? oz : 0, z1 = sz > 0 ? oz : 0;
+        const int y0 = sy < 0 ? oy : 0, y1 = sy > 0 ? oy : 0;
+        T wv[4][V], lo[4], hi[4];
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-        const bool first_lo = (v == 0) && has_lo;
-        const bool last_hi = (v == V - 1) && has_hi;
-        Acc s = first_lo ? Acc(lo[0]) + Acc(wv[0][v]) : Acc(wv[0][v]);
-        if (last_hi) s = s + Acc(hi[0]);
-#pragma unroll
-        for (int c = 1; c < 4; ++c) {
+        for (int c = 0; c < 4; ++c) {
             const int cz = c >> 1, cy = c & 1;
             const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
-            if (!valid) continue;
-            if (first_lo) s = s + Acc(lo[c]);
-            s = s + Acc(wv[c][v]);
-            if (last_hi) s = s + Acc(hi[c]);
+            const int off = l0 + (cz ? z1 : z0) + (cy ? y1 : y0);
+            if (valid) {
+                vload_nc<T, V>(w + off, wv[c]);
+                lo[c] = has_lo ? __ldg(w + off - (NP - N)) : T(0);              // element ex-1, node i = N
+                hi[c] = has_hi ? __ldg(w + off + (V - 1) + (NP - N)) : T(0);   // element ex+1, node i = 0
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) wv[c][v] = T(0);
+                lo[c] = hi[c] = T(0);
+            }
         }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const bool first_lo = (v == 0) && has_lo;
+            const bool last_hi = (v == V - 1) && has_hi;
+            T s = first_lo ? lo[0] + wv[0][v] : wv[0][v];
+            if (last_hi) s = s + hi[0];
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                const int cz = c >> 1, cy = c & 1;
+                const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
+                if (!valid) continue;
+                if (first_lo) s = s + lo[c];
+                s = s + wv[c][v];
+                if (last_hi) s = s + hi[c];
+            }
+            sv[v] = s;
+        }
+    }
+    T xv[V], pv[V], rv[V], dv[V];
+    if (!DX) {
+        vload<T, V>(x + l0, xv);
+        vload<T, V>(p + l0, pv);
+    }
+    vload<T, V>(r + l0, rv);
+    if (PRE) vload<T, V>(dinv + l0, dv);
+    const bool owner_row = sy >= 0 && sz >= 0;
+    Acc rr = Acc(0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
         const bool masked = (v == 0 && mask_lo) || (v == V - 1 && mask_hi);
         if (!masked) {
-            xv[v] = fma(alpha, pv[v], xv[v]);
-            rv[v] = fma(-alpha, T(s), rv[v]);
-            if (owner_row && !first_lo) {
+            if (!DX) xv[v] = fma(alpha, pv[v], xv[v]);
+            rv[v] = fma(-alpha, sv[v], rv[v]);
+            if (owner_row && !((v == 0) && has_lo)) {
                 if (PRE) {
                     // <r, M^-1 r> for beta and <r, r> for the stop test
                     acc = fma(Acc(rv[v]), Acc(dv[v] * rv[v]), acc);
@@ -222,11 +218,31 @@ __device__ __forceinline__ Acc update_vec(T *__restrict__ x, T *__restrict__ r, 
             }
         }
     }
-    vstore<T, V>(x + l0, xv);
+    if (!DX) vstore<T, V>(x + l0, xv);
     vstore<T, V>(r + l0, rv);
     if (PRE) *acc_rr += rr;
-    return acc;
 }
+
+// Row-class mapping of update vectors to threads: a warp takes the same row
+// (j, k) of EG consecutive elements, LR = (N+1)/V lanes per row, so every
+// lane of a warp is in the same face class in s and t (the gather branches
+// of update_vec are warp-uniform).  Returns the first local node of the
+// lane's vector, or -1 for an idle lane.
+template <int NQ, int V>
+struct RowMap {
+    static constexpr int NQ2 = NQ * NQ, NP = NQ2 * NQ;
+    static constexpr int LR = NQ / V;
+    static constexpr int EG = 32 / LR;
+    static __device__ __forceinline__ int l0(int task, int lane, int E) {
+        const int eg = task / NQ2;
+        const int row = task - eg * NQ2;
+        const int g = lane / LR, v = lane - g * LR;
+        const int e = eg * EG + g;
+        if (g >= EG || e >= E) return -1;
+        return e * NP + row * NQ + v * V;
+    }
+    static __host__ __device__ int tasks(int E) { return (E + EG - 1) / EG * NQ2; }
+};
 
 // b = mask(QQ^T f) on the box (copies summed in ascending local index).
 template <int NQ>
@@ -270,7 +286,35 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
     constexpr int V = UpdVec<NQ, T>::value;
     const int nv = nL / V;   // nL is a multiple of (N+1), hence of V
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nv; u += gridDim.x * blockDim.x)
-        acc += update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, nx, ny, nz, alpha);
+        update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, nx, ny, nz, alpha, acc);
+    const double bs = block_sum(double(acc), red);
+    if (publish_partial(bs, partials, &st->ticket_up)) {
+        const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
+        if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
+    }
+}
+
+// The same step with the row-class mapping (RowMap): used where the
+// arithmetic pipe, not HBM, bounds the update (FP64 on GB300).
+template <int NQ, typename T, typename Acc>
+__global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x, T *__restrict__ r,
+                                                              const T *__restrict__ p, const T *__restrict__ w,
+                                                              int nL, int nx, int ny, int nz, double *partials,
+                                                              CgState *st) {
+    __shared__ double red[32];
+    if (st->done) return;
+    constexpr int V = UpdVec<NQ, T>::value;
+    using RM = RowMap<NQ, V>;
+    const T alpha = T(st->alpha);
+    const int E = nL / RM::NP;
+    const int ntask = RM::tasks(E);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = int(gridDim.x * blockDim.x) >> 5;
+    Acc acc = Acc(0);
+    for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+        const int l0 = RM::l0(task, lane, E);
+        if (l0 >= 0) update_vec<NQ, V, T, Acc, false, true>(x, r, p, w, l0, nx, ny, nz, alpha, acc);
+    }
     const double bs = block_sum(double(acc), red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
@@ -281,6 +325,15 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
 template <int NQ, typename T, typename Acc>
 static int launch_update_rows_nq(const Problem *P, T *x, T *r, const T *p, const T *w, CgState *st) {
     constexpr int V = UpdVec<NQ, T>::value;
+    if constexpr (sizeof(T) == 8) {
+        using RM = RowMap<NQ, V>;
+        int64_t blocks = (int64_t(RM::tasks(int(P->E))) * 32 + 255) / 256;
+        if (blocks > 152 * 8) blocks = 152 * 8;
+        cg_update_class_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(
+            x, r, p, w, int(P->nL), P->nx, P->ny, P->nz, P->partials, st);
+        count_launches(1);
+        return cuda_check(cudaGetLastError(), "cg_update_class_kernel");
+    }
     int64_t blocks = (P->nL / V + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~13-27 vectors per thread at E = 32768, N = 7
     cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(P->nL), P->nx,

@@ -10,12 +10,17 @@
 //
 // CG (Nekbone without preconditioner, Section VIII-A).  One iteration is two
 // kernels:
-//   1. ax_f64_kernel<CG>: p = r + beta p; w = A_local p; <p, A p>; alpha
-//   2. cg_update_nodes_kernel (sem_box.cuh): every local node sums the copies
+//   1. the operator kernel in CG mode (the variant the tuner chose): the
+//      previous iteration's x += alpha p, then p = r + beta p; w = A_local p;
+//      <p, A p>; alpha
+//   2. cg_update_class_kernel (sem_box.cuh): every local node sums the copies
 //      of w of its global node in ascending local index (the direct-stiffness
-//      sum), then applies x += alpha p and r -= alpha (QQ^T w) to itself;
-//      <r, r> is accumulated once per global node; the last block forms rho,
-//      beta, the iteration count and the stop flag.
+//      sum), then applies r -= alpha (QQ^T w) to itself; <r, r> is
+//      accumulated once per global node; the last block forms rho, beta, the
+//      iteration count and the stop flag.
+// Moving x += alpha p into the next operator kernel (which has p in shared
+// memory anyway) takes 24 of the update's 48 bytes per node off HBM and one
+// FP64 operation off the update; x_finish_kernel applies the last one.
 // The dot products of the paper are tree reductions (Section VIII-B, the
 // unrolled reduction of Table "HIP-variable vs HIP-fixed"); here each block
 // reduces in a fixed order and the last block to finish sums the per-block
@@ -157,6 +162,22 @@ int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, dou
     return cuda_check(cudaGetLastError(), "cg_init_kernel");
 }
 
+// The last iteration's x += alpha p: the FP64 CG operator kernel applies an
+// iteration's x update at the start of the next iteration (it holds p there
+// anyway); the iteration that stopped the solve has no next one.
+__global__ void x_finish_kernel(double *__restrict__ x, const double *__restrict__ p, const CgState *st,
+                                int64_t n) {
+    const double alpha = st->alpha;
+    for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < n; l += int64_t(gridDim.x) * blockDim.x)
+        x[l] = fma(alpha, p[l], x[l]);
+}
+
+int launch_x_finish(const Problem *P) {
+    x_finish_kernel<<<stream_grid(P->nL), kThreads, 0, stream()>>>(P->x, P->p, P->st, P->nL);
+    count_launches(1);
+    return cuda_check(cudaGetLastError(), "x_finish_kernel");
+}
+
 int launch_cg_update(const Problem *P) {
     return launch_update_rows<double, double>(P, P->x, P->r, P->p, P->w, P->st);
 }
@@ -220,8 +241,10 @@ int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, doub
         if (*status_host() != 0) break;
         if (P->st_host->done) break;
     }
-    rc = cuda_check(cudaMemcpyAsync(P->st_host, P->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
-                    "cg: state read");
+    rc = launch_x_finish(P);
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(P->st_host, P->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
+                        "cg: state read");
     if (rc == SEM_OK && x != P->x)
         rc = cuda_check(cudaMemcpyAsync(x, P->x, sizeof(double) * P->nL, cudaMemcpyDeviceToDevice, stream()),
                         "cg: copy x");

@@ -105,8 +105,9 @@ enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
 // (one thread per (i, j) column, fixed elements per block), the line kernel
 // of sem_ax_lines.cuh (whole lines per thread, even-odd split, elements per
 // block chosen at launch), and the persistent TMA-pipelined column kernel of
-// sem_ax32p.cuh (FP32 only).
-enum AxVariant : int { kAxColumns = 0, kAxLines = 1, kAxPersistent = 2, kAxVariants = 3 };
+// sem_ax32p.cuh (FP32 only), and the line kernel with the geometric factors
+// loaded into registers before the slab wait (FP32 with BF16 factors only).
+enum AxVariant : int { kAxColumns = 0, kAxLines = 1, kAxPersistent = 2, kAxLinesPrefetch = 3, kAxVariants = 4 };
 // What is tuned: the FP64 operator, and the FP32 operator with FP32 or BF16
 // geometric factors.
 enum TuneKind : int { kTuneF64 = 0, kTuneF32G32 = 1, kTuneF32G16 = 2, kTuneKinds = 3 };
@@ -129,7 +130,7 @@ int tune_load(const char *path);
 // line-kernel launchers (sem_ax_lines64.cu, sem_ax_lines32.cu); mode 0: y = A x,
 // 1: CG operator on P's vectors, 2: Jacobi-PCG operator
 int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb);
-int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb);
+int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb, bool pf);
 bool lines_epb_ok(int nq, int epb, size_t elem_bytes);
 void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 
@@ -173,6 +174,7 @@ int launch_dot(const Problem *P, const double *u, const double *v);  // -> st->d
 int launch_sub(const Problem *P, const double *a, const double *b, double *out);  // out = a - b
 int launch_cg_init(const Problem *P, const double *b, int maxit, double tol, double *hist);
 int launch_cg_update(const Problem *P);
+int launch_x_finish(const Problem *P);       // x += alpha p of the last iteration (deferred update)
 int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, double *hist,
              int64_t *iters, double *rel_res);
 int launch_ax_pcg(const Problem *P);         // p = dinv r + beta p; w = A_local p; <p,w>

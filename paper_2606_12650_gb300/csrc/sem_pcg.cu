@@ -125,10 +125,17 @@ __global__ void __launch_bounds__(256) pcg_update_kernel(double *__restrict__ x,
     __shared__ double red[32];
     if (st->done) return;
     constexpr int V = UpdVec<NQ, double>::value;
+    using RM = RowMap<NQ, V>;
     const double alpha = st->alpha;
     double rz = 0.0, rr = 0.0;
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nL / V; u += gridDim.x * blockDim.x)
-        rz += update_vec<NQ, V, double, double, true>(x, r, p, w, u * V, nx, ny, nz, alpha, dinv, &rr);
+    const int E = nL / RM::NP;
+    const int ntask = RM::tasks(E);
+    const int lane = threadIdx.x & 31;
+    const int nwarps = int(gridDim.x * blockDim.x) >> 5;
+    for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
+        const int l0 = RM::l0(task, lane, E);
+        if (l0 >= 0) update_vec<NQ, V, double, double, true, true>(x, r, p, w, l0, nx, ny, nz, alpha, rz, dinv, &rr);
+    }
     const double s0 = block_sum(rz, red);
     const double s1 = block_sum(rr, red);
     if (publish_partial2(s0, s1, partials, &st->ticket_up)) {
@@ -141,8 +148,8 @@ __global__ void __launch_bounds__(256) pcg_update_kernel(double *__restrict__ x,
 template <int NQ>
 static int launch_pcg_update_nq(const Problem *P) {
     constexpr int V = UpdVec<NQ, double>::value;
-    int64_t blocks = (P->nL / V + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    int64_t blocks = (int64_t(RowMap<NQ, V>::tasks(int(P->E))) * 32 + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
     pcg_update_kernel<NQ><<<unsigned(blocks), 256, 0, stream()>>>(P->x, P->r, P->p, P->w, P->dinv, int(P->nL),
                                                                   P->nx, P->ny, P->nz, P->partials, P->st);
     count_launches(1);
@@ -217,8 +224,10 @@ int pcg_solve(Problem *P, const double *b, double *x, double tol, int maxit, dou
         if (rc != SEM_OK) return rc;
         if (*status_host() != 0 || P->st_host->done) break;
     }
-    rc = cuda_check(cudaMemcpyAsync(P->st_host, P->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
-                    "pcg: state read");
+    rc = launch_x_finish(P);   // the last iteration's deferred x += alpha p
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(P->st_host, P->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
+                        "pcg: state read");
     if (rc == SEM_OK && x != P->x)
         rc = cuda_check(cudaMemcpyAsync(x, P->x, sizeof(double) * P->nL, cudaMemcpyDeviceToDevice, stream()),
                         "pcg: copy x");

@@ -26,21 +26,25 @@ TuneChoice g_tab[kTuneKinds][kMaxQ + 1];
 bool g_init = false;
 uint64_t g_epoch = 1;
 
-// Built-in table: the winners of a tuning run on GB300 with ~17 M local
+// Built-in table: the winners of tuning runs on GB300 with ~17 M local
 // nodes per problem (E = 64^3 at N = 3 down to 26^3 at N = 9; CG operator,
-// 10 launches per candidate).  Elements per block for N = 1..9; 0 = the
-// kind's column (FP64) or persistent (FP32) kernel.
-constexpr int kDefaultEpb[kTuneKinds][kMaxQ + 1] = {
-    {0, 0, 0, 0, 0, 15, 7, 7, 8, 6, 5},      // FP64
-    {0, 0, 0, 0, 0, 20, 14, 10, 0, 4, 5},    // FP32, FP32 G
-    {0, 0, 0, 0, 0, 20, 14, 10, 6, 6, 5},    // FP32, BF16 G
+// 10 launches per candidate), as {variant, elements per block} for
+// N = 1..9; the run-time tuner replaces entries for the problems at hand.
+struct DefaultEntry {
+    int variant, epb;
+};
+constexpr DefaultEntry kDefault[kTuneKinds][kMaxQ + 1] = {
+    // FP64
+    {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 15}, {1, 7}, {1, 7}, {1, 4}, {1, 6}, {1, 5}},
+    // FP32, FP32 factors
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 8}, {1, 4}, {1, 5}},
+    // FP32, BF16 factors
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {3, 20}, {3, 7}, {1, 10}, {3, 4}, {1, 6}, {3, 3}},
 };
 
 TuneChoice default_choice(int kind, int nq) {
-    const int epb = (kind >= 0 && kind < kTuneKinds && nq >= 0 && nq <= kMaxQ) ? kDefaultEpb[kind][nq] : 0;
-    if (epb > 0) return {kAxLines, epb, 0.0};
-    if (kind == kTuneF64) return {kAxColumns, 0, 0.0};
-    return {kAxPersistent, 0, 0.0};
+    if (kind < 0 || kind >= kTuneKinds || nq < 0 || nq > kMaxQ) return {kAxColumns, 0, 0.0};
+    return {kDefault[kind][nq].variant, kDefault[kind][nq].epb, 0.0};
 }
 
 void ensure_init() {
@@ -58,21 +62,27 @@ bool choice_ok(int kind, int nq, const TuneChoice &c) {
         case kAxColumns: return kind == kTuneF64;
         case kAxPersistent: return kind != kTuneF64;
         case kAxLines: return lines_epb_ok(nq, c.epb, elem_bytes(kind));
+        case kAxLinesPrefetch: return kind == kTuneF32G16 && lines_epb_ok(nq, c.epb, elem_bytes(kind));
         default: return false;
     }
 }
 
 // The candidates for (kind, nq): the kind's column kernel, then the line
-// kernel with ~64 .. 512 threads per block.
+// kernel with ~64 .. 512 threads per block (and, for BF16 factors, the same
+// with the factors prefetched).
 int candidates(int kind, int nq, TuneChoice *out, int cap) {
     int n = 0;
     out[n++] = {kind == kTuneF64 ? kAxColumns : kAxPersistent, 0, 0.0};
-    int prev = 0;
-    for (int t : {64, 128, 192, 256, 384, 512}) {
-        int epb = t / (nq * nq);
-        if (epb < 1) epb = 1;
-        if (epb != prev && lines_epb_ok(nq, epb, elem_bytes(kind)) && n < cap) out[n++] = {kAxLines, epb, 0.0};
-        prev = epb;
+    const int nv = kind == kTuneF32G16 ? 2 : 1;
+    for (int v = 0; v < nv; ++v) {
+        int prev = 0;
+        for (int t : {64, 128, 192, 256, 384, 512}) {
+            int epb = t / (nq * nq);
+            if (epb < 1) epb = 1;
+            if (epb != prev && lines_epb_ok(nq, epb, elem_bytes(kind)) && n < cap)
+                out[n++] = {v == 0 ? kAxLines : kAxLinesPrefetch, epb, 0.0};
+            prev = epb;
+        }
     }
     return n;
 }
@@ -80,12 +90,13 @@ int candidates(int kind, int nq, TuneChoice *out, int cap) {
 template <typename T>
 __global__ void tune_fill_kernel(T *r, T *p, int64_t n) {
     for (int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < n; q += int64_t(gridDim.x) * blockDim.x) {
-        r[q] = T(1);
+        r[q] = T(1 + (q & 7) * 0.125);
         p[q] = T(0);
     }
 }
 
 __global__ void tune_state_kernel(CgState *st) {
+    st->alpha = 0.0;
     st->beta = 0.0;
     st->rho = 1.0;
     st->done = 0;
@@ -188,7 +199,7 @@ int tune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return set_error(SEM_EARG, std::string("autotune_save: cannot write ") + path);
     fprintf(f, "# libsem operator table: kind(0 fp64, 1 fp32/fp32 G, 2 fp32/bf16 G) N variant(0 columns, "
-               "1 lines, 2 persistent) elements_per_block us\n");
+               "1 lines, 2 persistent, 3 lines with G prefetch) elements_per_block us\n");
     for (int k = 0; k < kTuneKinds; ++k)
         for (int q = 2; q <= kMaxQ; ++q) {
             const TuneChoice &c = g_tab[k][q];
