@@ -497,6 +497,18 @@ def run_batched(a, job, rank, stream, sem, torch):
         m.mask(f)
         meshes.append(m)
         bs.append(f)
+    # per-order tuner: each order of the mix tuned on its largest problem (FP64
+    # and the mixed path's FP32/BF16 operator); the batch takes its operator
+    # body and elements per item from the resulting table
+    tuned = {}
+    if not a.no_tune:
+        for N in sorted({m.N for m in meshes}):
+            big = max((m for m in meshes if m.N == N), key=lambda m: m.E)
+            tuned[N] = {}
+            for kind, name in ((sem.TUNE_F64, "fp64"), (sem.TUNE_F32_G16, "fp32_bf16")):
+                big.autotune(kind, reps=5)
+                v, e, us = sem.autotune_get(kind, N)
+                tuned[N][name] = {"variant": VARIANTS[v], "epb": e, "us": us, "tuned_on_E": big.E}
     B = Batch(meshes)
     b_all = torch.cat(bs)
     del bs
@@ -505,7 +517,7 @@ def run_batched(a, job, rank, stream, sem, torch):
     gdof_per_iter = np.array([m.E * m.N ** 3 for m in meshes], dtype=np.float64)
     out = {"workload": f"{len(meshes)} problems, E log-uniform [8, 4096] (near-cubic boxes), N in {{3,5,7,9}}, "
                        f"jitter 5%, random RHS; tol {a.tol:g}; every CG phase one persistent launch",
-           "problems": len(meshes), "local_dofs_total": int(B.nL_total),
+           "problems": len(meshes), "local_dofs_total": int(B.nL_total), "tuned_per_order": tuned,
            "E_total": int(sum(m.E for m in meshes)), "setup_s": setup_s}
     for mode, name in ((0, "fp64"), (1, "mixed_bf16")):
         B.solve(b_all, x_all, a.tol, a.maxit, mode, a.inner_tol)    # warm-up (graph capture)

@@ -124,11 +124,22 @@ struct LineShape {
     }
 };
 
+// One group of ne (<= epb) elements starting at element e0, for a block of
+// at least epb (N+1)^2 threads.  regA: 16-byte aligned shared memory of
+// 3 LineShape::region(N+1, epb) values; bar: an initialised mbarrier whose
+// next completion is phase `phase`; cd, ct: even-odd coefficients of D and
+// D^T.  CG mode: p = r + beta p (PRE: M^-1 r + beta p), and xs += xalpha p_old
+// first when xs is given; *part receives this thread's <p, A_local p> partial
+// (in T).  Returns false if the slab copy timed out (status set, copies
+// drained).
 // PF (BF16 factors only): the element's geometric factors are loaded into
 // registers (3 words per node) before the slab wait, so their latency
 // overlaps the TMA copy instead of stalling phase 2.
-template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF = false>
-__global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P) {
+template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF>
+__device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G, const EoMat<T> &cd,
+                                            const EoMat<T> &ct, T beta, T xalpha, T *xs, const T *dinv, int64_t e0,
+                                            int ne, int epb, T *regA, uint64_t *bar, uint32_t phase,
+                                            int32_t *status, T *part) {
     static_assert(!PF || sizeof(GT) == 2, "G prefetch is for BF16 factors");
     constexpr int NQ2 = NQ * NQ, NP = NQ2 * NQ;
     constexpr int P1 = LinePad<NQ>::P1, P2 = LinePad<NQ>::P2, NPP = LinePad<NQ>::NPP;
@@ -139,28 +150,16 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     // or row / 2; columns of one warp differ in k, hence the rotation by k.
     constexpr bool ROT = NQ == 8;
     constexpr int RPB = sizeof(T) == 8 ? 2 : 4;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
-    const AxArgs<T, GT> &A = P.a;
-    if (CG && A.st->done) return;  // solve finished: the rest of the graph is a no-op
-
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    const int RG = LineShape::region(NQ, P.epb, int(sizeof(T)));
-    T *regA = reinterpret_cast<T *>(smem + 16);
+    const int RG = LineShape::region(NQ, epb, int(sizeof(T)));
     T *regB = regA + RG;
     T *regC = regB + RG;
     const int tid = threadIdx.x;
     const int nthreads = blockDim.x;
-    const int64_t e0 = int64_t(blockIdx.x) * P.epb;
-    const int ne = int(min(int64_t(P.epb), A.E - e0));
-
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
 
     // ---- (0) stage the slab(s): TMA for the aligned middle, plain loads for the edges
     const uint32_t bytes = uint32_t(ne) * NP * uint32_t(sizeof(T));
-    const T *src1 = A.x + e0 * NP;                 // x (plain) or r (CG)
-    const T *src2 = CG ? A.p + e0 * NP : nullptr;  // p (CG)
+    const T *src1 = x + e0 * NP;                 // x (plain) or r (CG)
+    const T *src2 = CG ? p + e0 * NP : nullptr;  // p (CG)
     T *s1 = slab_dst(regA, src1);
     T *s2 = CG ? slab_dst(regB, src2) : nullptr;
     const SlabPlan pl1 = slab_plan(src1, bytes);
@@ -184,16 +183,16 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     if (PF && act) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
-            const unsigned *gq = reinterpret_cast<const unsigned *>(A.G + 6 * (nb + k * NQ2 + b * NQ + a));
+            const unsigned *gq = reinterpret_cast<const unsigned *>(G + 6 * (nb + k * NQ2 + b * NQ + a));
             gw[k][0] = __ldg(gq);
             gw[k][1] = __ldg(gq + 1);
             gw[k][2] = __ldg(gq + 2);
         }
     }
-    const bool ok = mbar_wait_bounded(bar, 0u, A.status);
+    const bool ok = mbar_wait_bounded(bar, phase, status);
     if (__syncthreads_or(!ok)) {
-        mbar_wait_bounded(bar, 0u, nullptr);  // let copies in flight land before leaving
-        return;
+        mbar_wait_bounded(bar, phase, nullptr);  // let copies in flight land before leaving
+        return false;
     }
 
     const int rq = b * NQ2 + a * NQ;   // r line (j, k) = (a, b) of the slab: first node
@@ -205,18 +204,16 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
 
     T xk[NQ];
     if (CG) {
-        const T beta = T(A.st->beta);
-        const T xalpha = T(A.st->alpha);   // read before this launch's last block replaces it
         if (act) {
 #pragma unroll
             for (int k = 0; k < NQ; ++k) {
                 const int q = eb * NP + k * NQ2 + tq;
-                const T zq = PRE ? A.dinv[nb + k * NQ2 + tq] * s1[q] : s1[q];
-                if (A.xs) A.xs[nb + k * NQ2 + tq] = fma(xalpha, s2[q], A.xs[nb + k * NQ2 + tq]);
+                const T zq = PRE ? dinv[nb + k * NQ2 + tq] * s1[q] : s1[q];
+                if (xs) xs[nb + k * NQ2 + tq] = fma(xalpha, s2[q], xs[nb + k * NQ2 + tq]);
                 const T pn = fma(beta, s2[q], zq);
                 s2[q] = pn;
                 xk[k] = pn;
-                A.p[nb + k * NQ2 + tq] = pn;
+                p[nb + k * NQ2 + tq] = pn;
             }
         }
         __syncthreads();
@@ -231,7 +228,7 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     // ---- (1) gradient lines
     T ut[NQ];
     if (act) {
-        T u[NQ], y[NQ];
+        T u[NQ], yl[NQ];
         if (ROT) {
             const int R = (ab / RPB) & (NQ - 1);
 #pragma unroll
@@ -241,9 +238,9 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
 #pragma unroll
             for (int l = 0; l < NQ; ++l) u[l] = SX[rq + l];
         }
-        eo_apply<NQ, T>(u, y, P.d);
+        eo_apply<NQ, T>(u, yl, cd);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rp + l] = y[l];
+        for (int l = 0; l < NQ; ++l) SU[rp + l] = yl[l];
         if (ROT) {
             const int R = b & (NQ - 1);
 #pragma unroll
@@ -253,10 +250,10 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
 #pragma unroll
             for (int l = 0; l < NQ; ++l) u[l] = SX[cq + l * NQ];
         }
-        eo_apply<NQ, T>(u, y, P.d);
+        eo_apply<NQ, T>(u, yl, cd);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = y[l];
-        eo_apply<NQ, T>(xk, ut, P.d);
+        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = yl[l];
+        eo_apply<NQ, T>(xk, ut, cd);
     }
     __syncthreads();
 
@@ -273,7 +270,7 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
                              g45 = bf16x2_to_float2(gw[k][2]);
                 g[0] = g01.x; g[1] = g01.y; g[2] = g23.x; g[3] = g23.y; g[4] = g45.x; g[5] = g45.y;
             } else {
-                load_g6(A.G, nb + k * NQ2 + tq, g);
+                load_g6(G, nb + k * NQ2 + tq, g);
             }
             SU[pq] = g[0] * ur + g[1] * us + g[2] * ut[k];
             SV[pq] = g[1] * ur + g[3] * us + g[4] * ut[k];
@@ -285,18 +282,18 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     // ---- (3) divergence lines (in place: each line has one owner)
     T yt[NQ];
     if (act) {
-        T u[NQ], y[NQ];
+        T u[NQ], yl[NQ];
 #pragma unroll
         for (int l = 0; l < NQ; ++l) u[l] = SU[rp + l];
-        eo_apply<NQ, T>(u, y, P.dt);
+        eo_apply<NQ, T>(u, yl, ct);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rp + l] = y[l];
+        for (int l = 0; l < NQ; ++l) SU[rp + l] = yl[l];
 #pragma unroll
         for (int l = 0; l < NQ; ++l) u[l] = SV[cp + l * P1];
-        eo_apply<NQ, T>(u, y, P.dt);
+        eo_apply<NQ, T>(u, yl, ct);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = y[l];
-        eo_apply<NQ, T>(wt, yt, P.dt);
+        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = yl[l];
+        eo_apply<NQ, T>(wt, yt, ct);
     }
     __syncthreads();
 
@@ -307,16 +304,39 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
         for (int k = 0; k < NQ; ++k) {
             const int pq = k * P2 + tp;
             const T yv = (SU[pq] + SV[pq]) + yt[k];
-            A.y[nb + k * NQ2 + tq] = yv;
+            y[nb + k * NQ2 + tq] = yv;
             if (CG) acc = fma(SX[k * NQ2 + tq], yv, acc);
         }
     }
+    if (CG) *part = acc;
+    return true;
+}
+
+template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF = false>
+__global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[32];
+    const AxArgs<T, GT> &A = P.a;
+    if (CG && A.st->done) return;  // solve finished: the rest of the graph is a no-op
+
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    T *regA = reinterpret_cast<T *>(smem + 16);
+    const int64_t e0 = int64_t(blockIdx.x) * P.epb;
+    const int ne = int(min(int64_t(P.epb), A.E - e0));
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    const T beta = CG ? T(A.st->beta) : T(0);
+    const T xalpha = CG ? T(A.st->alpha) : T(0);   // read before this launch's last block replaces it
+    T part = T(0);
+    if (!lines_group<NQ, T, GT, CG, PRE, PF>(A.x, A.y, A.p, A.G, P.d, P.dt, beta, xalpha, CG ? A.xs : nullptr,
+                                             A.dinv, e0, ne, P.epb, regA, bar, 0u, A.status, &part))
+        return;
     if (CG) {
         // the thread's partial is formed in T; the block and grid sums are FP64
-        const double bs = block_sum(double(acc), red);
+        const double bs = block_sum(double(part), red);
         if (publish_partial(bs, A.partials, &A.st->ticket_ax)) {
             const double pap = finish_partials(A.partials, int(gridDim.x), &A.st->ticket_ax, red);
-            if (tid == 0) {
+            if (threadIdx.x == 0) {
                 A.st->pap = pap;
                 A.st->alpha = A.st->rho / pap;
             }

@@ -2,11 +2,14 @@
 // orders solved together: each CG phase is ONE persistent launch over all
 // problems, replayed from a CUDA graph.
 //
-// Work lists.  Every problem is cut into operator items (groups of up to EPB(N)
-// elements, EPB(N) = 256 / (N+1)^2) and vector items (row-aligned runs of
-// ~4096 local nodes).  A persistent kernel's CTAs take items from a global
-// counter (dynamic load balance across problems of very different cost); a
-// device-side switch on N dispatches to the body compiled for that order.
+// Work lists.  Every problem is cut into operator items (groups of elements)
+// and vector items (row-aligned runs of ~4096 local nodes).  A persistent
+// kernel's CTAs take items from a global counter (dynamic load balance across
+// problems of very different cost); a device-side switch on N dispatches to
+// the body compiled for that order.  The operator body and the elements per
+// item follow the per-order tuner's table for the batch's precision: the
+// line body (sem_ax_lines.cuh) with the tuned elements per group, capped at
+// what 256 threads hold, or the column body with 256 / (N+1)^2 elements.
 //
 // Per-problem reductions.  Each item writes one partial (fixed-order block
 // tree) to its own slot; the problem's last item to finish (per-problem
@@ -32,7 +35,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "sem_ax_kernel.cuh"
+#include "sem_ax_lines.cuh"
 #include "sem_box.cuh"
 #include "sem_device.cuh"
 #include "sem_internal.h"
@@ -68,7 +71,7 @@ struct BatchItem {
     int prob, nq;
     int64_t first;  // first element (operator) or first local node (vector)
     int count;      // elements or nodes
-    int pad;
+    int lines;      // operator items: 1 = line body, 0 = column body
 };
 
 struct BatchQueue {
@@ -111,9 +114,11 @@ struct BEpb {
 };
 
 template <typename T>
-constexpr size_t batch_ax_smem() {
+size_t batch_ax_smem() {
     size_t m = 0;
-#define SEM_BS(Q) m = std::max(m, AxShape<Q, BEpb<Q>::value, T>::SMEM);
+#define SEM_BS(Q)                                          \
+    m = std::max(m, AxShape<Q, BEpb<Q>::value, T>::SMEM);  \
+    m = std::max(m, LineShape::smem(Q, BEpb<Q>::value, int(sizeof(T))));
     SEM_BS(2) SEM_BS(3) SEM_BS(4) SEM_BS(5) SEM_BS(6) SEM_BS(7) SEM_BS(8) SEM_BS(9) SEM_BS(10)
 #undef SEM_BS
     return m;
@@ -124,6 +129,16 @@ constexpr size_t batch_ax_smem() {
 // constant and the products read constant-bank operands directly.
 __constant__ double c_D64[kMaxQ - 1][kMaxQ * kMaxQ];
 __constant__ float c_D32[kMaxQ - 1][kMaxQ * kMaxQ];
+// even-odd coefficients of D ([0]) and D^T ([1]) for the line body
+__constant__ EoMat<double> c_E64[kMaxQ - 1][2];
+__constant__ EoMat<float> c_E32[kMaxQ - 1][2];
+
+template <typename T>
+__device__ __forceinline__ const EoMat<T> &const_eo(int nq, int which);
+template <>
+__device__ __forceinline__ const EoMat<double> &const_eo<double>(int nq, int which) { return c_E64[nq - 2][which]; }
+template <>
+__device__ __forceinline__ const EoMat<float> &const_eo<float>(int nq, int which) { return c_E32[nq - 2][which]; }
 
 template <int NQ, typename T>
 struct ConstD;
@@ -198,6 +213,16 @@ __device__ __noinline__ bool batch_ax_item(const T *xin, T *yout, T *pv, const G
                                                    bar, phase, status, pt);
 }
 
+template <int NQ, typename T, typename GT, bool CG>
+__device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
+                                              int count, T *regA, uint64_t *bar, uint32_t phase, int32_t *status,
+                                              T *pt) {
+    constexpr bool PF = sizeof(GT) == 2;   // BF16 factors: prefetched into registers
+    return lines_group<NQ, T, GT, CG, false, PF>(xin, yout, pv, G, const_eo<T>(NQ, 0), const_eo<T>(NQ, 1), beta,
+                                                 T(0), nullptr, nullptr, first, count, count, regA, bar, phase,
+                                                 status, pt);
+}
+
 // mode: 0 = FP64 CG (p = r + beta p, w = A p), 1 = FP64 plain (w = A x),
 //       2 = FP32 inner CG on the FP32 vectors
 template <typename T, typename GT, int MODE>
@@ -234,8 +259,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
         switch (item.nq) {
 #define SEM_BAX(Q)                                                                                     \
     case Q:                                                                                            \
-        ok = batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count, regA, bar,     \
-                                         phase, status, &pt);                                          \
+        ok = item.lines ? batch_lines_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count, \
+                                                         regA, bar, phase, status, &pt)                  \
+                        : batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,    \
+                                                      regA, bar, phase, status, &pt);                    \
         break;
             SEM_BAX(2) SEM_BAX(3) SEM_BAX(4) SEM_BAX(5) SEM_BAX(6) SEM_BAX(7) SEM_BAX(8) SEM_BAX(9) SEM_BAX(10)
 #undef SEM_BAX
@@ -464,7 +491,7 @@ static int batch_grid(const void *kern, size_t smem, int *out) {
 
 template <typename T, typename GT, int MODE>
 static int launch_bax(Batch *B, int grid) {
-    constexpr size_t sm = batch_ax_smem<T>();
+    const size_t sm = batch_ax_smem<T>();
     const int g = std::max(1, std::min(grid, B->n_ax));
     batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(
         B->d_probs, B->d_ax, B->n_ax, B->part, B->tickets, B->ctl, status_word());
@@ -499,8 +526,22 @@ static int batch_attrs(Batch *B) {
             gll_rule_and_derivative(N, xi, w, h64[N - 1]);
             for (int q = 0; q < (N + 1) * (N + 1); ++q) h32[N - 1][q] = float(h64[N - 1][q]);
         }
+        static EoMat<double> e64[kMaxQ - 1][2];
+        static EoMat<float> e32[kMaxQ - 1][2];
+        for (int N = 1; N <= kMaxQ - 1; ++N) {
+            const int nq = N + 1;
+            double Dt[kMaxQ * kMaxQ];
+            for (int i = 0; i < nq; ++i)
+                for (int l = 0; l < nq; ++l) Dt[i * nq + l] = h64[N - 1][l * nq + i];
+            e64[N - 1][0] = eo_coefficients<double>(h64[N - 1], nq);
+            e64[N - 1][1] = eo_coefficients<double>(Dt, nq);
+            e32[N - 1][0] = eo_coefficients<float>(h64[N - 1], nq);
+            e32[N - 1][1] = eo_coefficients<float>(Dt, nq);
+        }
         int rc = cuda_check(cudaMemcpyToSymbol(c_D64, h64, sizeof h64), "batch: D table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_D32, h32, sizeof h32), "batch: D table");
+        if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E64, e64, sizeof e64), "batch: even-odd table");
+        if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E32, e32, sizeof e32), "batch: even-odd table");
         const int a = int(batch_ax_smem<double>()), f = int(batch_ax_smem<float>());
         if (rc == SEM_OK)
             rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 0>,
@@ -604,10 +645,14 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
             q.outer_done = 0;
             any_init = true;
         }
-        const int epb = kBatchThreads / (P->nq * P->nq);
+        // operator body and elements per item from the tuner's table
+        const int full = kBatchThreads / (P->nq * P->nq);
+        const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
+        const int lines = (c.variant == kAxLines || c.variant == kAxLinesPrefetch) ? 1 : 0;
+        const int epb = lines ? std::max(1, std::min(c.epb, full)) : full;
         q.ax_first = int(ax.size());
         for (int64_t e = 0; e < P->E; e += epb)
-            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(epb, P->E - e)), 0});
+            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(epb, P->E - e)), lines});
         q.ax_count = int(ax.size()) - q.ax_first;
         const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
         q.vec_first = int(vec.size());

@@ -69,6 +69,46 @@ def test_batch_reaches_tolerance_per_problem(semlib, oracle_mod, mode):
         m.free()
 
 
+class _body:
+    """Make the batch use the column (or line) operator body for every order
+    of the spec list, by setting the per-order tuner table; restore after."""
+
+    def __init__(self, mode, variant):
+        self.kind = 0 if mode == 0 else (2 if mode == 1 else 1)
+        self.variant = variant
+
+    def __enter__(self):
+        from paper_2606_12650_gb300 import sem
+        self.old = {N: sem.autotune_get(self.kind, N) for N in range(1, 10)}
+        for N in range(1, 10):
+            if self.variant == "columns":
+                sem.autotune_set(self.kind, N, 0 if self.kind == 0 else 2, 0)
+            else:
+                sem.autotune_set(self.kind, N, 1, max(1, 256 // (N + 1) ** 2))
+
+    def __exit__(self, *exc):
+        from paper_2606_12650_gb300 import sem
+        for N, (v, e, _) in self.old.items():
+            sem.autotune_set(self.kind, N, v, e)
+
+
+@pytest.mark.parametrize("body", ["columns", "lines"])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_body_reaches_tolerance(semlib, oracle_mod, mode, body):
+    """Each operator body of the batch engine (column or line) on the
+    nine-problem mix: tolerance met per problem, checked with the oracle."""
+    meshes, probs, bs = _build(oracle_mod, SPECS)
+    with _body(mode, body):
+        its, res, xs = _solve(meshes, bs, 1e-9, mode)
+    for k, (P, b, x) in enumerate(zip(probs, bs, xs)):
+        if not np.any(b):
+            continue
+        assert res[k] <= 1e-9, (k, res[k])
+        assert P.true_residual(b, x) <= 1.5e-9, k
+    for m in meshes:
+        m.free()
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 def test_batch_invariance_alone_vs_in_the_mix(semlib, oracle_mod, mode):
     """Problem 3 alone and inside the nine-problem batch: identical bits."""
