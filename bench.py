@@ -282,7 +282,7 @@ def run_ours(a):
     ax_ms = e0.elapsed_time(e1) / a.ax_reps
     flops = E * ax_flops_per_elem(N)
     achieved = flops / (ax_ms * 1e-3) / 1e9
-    bytes_alg = E * (N + 1) ** 3 * 80  # r, p in; p, w out; 6 geometric factors (FP64)
+    bytes_alg = E * (N + 1) ** 3 * 96  # r, p, x in; p, w, x out (x: the deferred update); 6 FP64 factors
     fp64 = sem.OutDouble()
     sem.run("peak_fma", 0, 4096, fp64)
     traffic = None
