@@ -14,6 +14,7 @@
 // which makes every copy's sum bit-identical.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 
 namespace sem {
@@ -322,20 +323,38 @@ __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x,
     }
 }
 
+// Blocks of an update launch, grid-stride beyond.  Measured on GB300 at
+// E = 32^3, N = 7: the FP32 update is fastest with one resident wave
+// (inner CG iteration 216 -> 190 us); the FP64 update with 8 blocks per SM
+// (230 us; one wave of 5 per SM: 293 us; one vector per thread, 32768
+// blocks: 340 us -- each block's FP64 reduction costs more than the latency
+// it hides).
+template <typename K>
+static int64_t resident_blocks(K kern, int threads) {
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 4;
+        }
+    }
+    return int64_t(per_sm) * sm_count();
+}
+
 template <int NQ, typename T, typename Acc>
 static int launch_update_rows_nq(const Problem *P, T *x, T *r, const T *p, const T *w, CgState *st) {
     constexpr int V = UpdVec<NQ, T>::value;
     if constexpr (sizeof(T) == 8) {
         using RM = RowMap<NQ, V>;
         int64_t blocks = (int64_t(RM::tasks(int(P->E))) * 32 + 255) / 256;
-        if (blocks > 152 * 8) blocks = 152 * 8;
+        blocks = std::min<int64_t>(blocks, int64_t(sm_count()) * 8);
         cg_update_class_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(
             x, r, p, w, int(P->nL), P->nx, P->ny, P->nz, P->partials, st);
         count_launches(1);
         return cuda_check(cudaGetLastError(), "cg_update_class_kernel");
     }
     int64_t blocks = (P->nL / V + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;   // grid-stride: ~13-27 vectors per thread at E = 32768, N = 7
+    blocks = std::min(blocks, resident_blocks(cg_update_nodes_kernel<NQ, T, Acc>, 256));
     cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(P->nL), P->nx,
                                                                                P->ny, P->nz, P->partials, st);
     count_launches(1);

@@ -12,6 +12,7 @@
 // kernel reduces both <r, M^-1 r> (beta) and <r, r> (stop test).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "sem_box.cuh"
@@ -149,7 +150,7 @@ template <int NQ>
 static int launch_pcg_update_nq(const Problem *P) {
     constexpr int V = UpdVec<NQ, double>::value;
     int64_t blocks = (int64_t(RowMap<NQ, V>::tasks(int(P->E))) * 32 + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    blocks = std::min<int64_t>(blocks, int64_t(sm_count()) * 8);
     pcg_update_kernel<NQ><<<unsigned(blocks), 256, 0, stream()>>>(P->x, P->r, P->p, P->w, P->dinv, int(P->nL),
                                                                   P->nx, P->ny, P->nz, P->partials, P->st);
     count_launches(1);
