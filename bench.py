@@ -20,6 +20,11 @@ Also reported on the same JSON line:
                 its own HBM roofline, solves/s against FP64, and a 1e-10 leg
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload
   clocks        nvidia-smi samples taken during the timed region
+  autotune      the per-order operator tuner's candidates and choices
+  pcg           the same solve with the Jacobi preconditioner
+  batched       256 uneven problems, each CG phase one persistent launch
+  serve         Poisson arrivals at 100..5000 req/s: p50/p99 latency, solves/s
+  paper_sweep   the paper's protocol: GDOF/s against E = 2^1..2^14, N = 4, 6, 8
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): every rank solves an independent problem (replicas,
@@ -81,10 +86,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=200, help="requests per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests per arrival rate")
     ap.add_argument("--serve-rates", default="100,200,500,1000,2000,5000")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-tune", action="store_true", help="keep the built-in operator table")
+    ap.add_argument("--no-paper-sweep", action="store_true", help="skip the N in {4,6,8}, E = 2^1..2^14 sweep")
     ap.add_argument("--tune-reps", type=int, default=10, help="timed launches per tuner candidate")
     return ap.parse_args()
 
@@ -349,6 +355,11 @@ def run_ours(a):
                               "mixed precision (BF16 G), 40 GB admission budget, 8 CG iterations per round",
                   "rates": rows}
 
+    # ---- the paper's own protocol: GDOF/s against E for N = 4, 6, 8
+    sweep_paper = None
+    if not a.no_paper_sweep and rank == 0:
+        sweep_paper = run_paper_sweep(a, stream, sem, torch)
+
     # ---- end to end through the public API, host buffers
     e2e = None
     if not a.no_e2e:
@@ -394,6 +405,7 @@ def run_ours(a):
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "pcg": pcg, "mixed": mixed, "batched": batched, "serve": served, "autotune": tune,
+                "paper_sweep": sweep_paper,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
                            "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
@@ -501,6 +513,7 @@ def run_batched(a, job, rank, stream, sem, torch):
     # and the mixed path's FP32/BF16 operator); the batch takes its operator
     # body and elements per item from the resulting table
     tuned = {}
+    saved = {(k, N): sem.autotune_get(k, N) for k in (sem.TUNE_F64, sem.TUNE_F32_G16) for N in range(1, 10)}
     if not a.no_tune:
         for N in sorted({m.N for m in meshes}):
             big = max((m for m in meshes if m.N == N), key=lambda m: m.E)
@@ -533,8 +546,47 @@ def run_batched(a, job, rank, stream, sem, torch):
                      "iters_total": int(its.sum()), "iters_max": int(its.max()), "max_rel_res": float(res.max())}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed_bf16"]["ms"]
     B.free()
+    for (k, N), (v, e, _) in saved.items():      # the later legs use the table tuned on the main problem
+        sem.autotune_set(k, N, v, e)
     for m in meshes:
         m.free()
+    return out
+
+
+def run_paper_sweep(a, stream, sem, torch):
+    """The paper's Nekbone protocol (Section VIII-B): unpreconditioned CG, N in
+    {4, 6, 8}, E = 2^1 .. 2^14 (near-cubic boxes, jitter 5 %, sine source),
+    100 iterations timed after 100 warm-up iterations, mean of 5; GDOF/s =
+    E N^3 100 / t.  Each timed solve includes its initialisation kernel and
+    the host's polling of the stop flag."""
+    from paper_2606_12650_gb300 import Mesh
+    from paper_2606_12650_gb300.inputs import box_vertices, near_cubic
+    out = {"workload": "CG 100 iterations (no tolerance), N in {4,6,8}, E = 2^1..2^14 near-cubic, jitter 5%, "
+                       "sine source; 100 warm-up iterations, mean of 5 timed solves", "gdofs": {}, "saturation_E": {}}
+    for N in (4, 6, 8):
+        row = {}
+        for k in range(1, 15):
+            E = 2 ** k
+            nx, ny, nz = near_cubic(E)
+            jit = 0.05 if min(nx, ny, nz) > 1 else 0.0
+            M = Mesh(nx, ny, nz, N, box_vertices(nx, ny, nz, jit, seed=1))
+            b = torch.empty(M.nL, dtype=torch.float64, device="cuda")
+            M.rhs_sin(b)
+            x = torch.empty_like(b)
+            M.cg_solve(b, x, 0.0, 100)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(5):
+                M.cg_solve(b, x, 0.0, 100)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 5 * 1e-3
+            row[E] = E * N ** 3 * 100 / t / 1e9
+            M.free()
+        out["gdofs"][N] = row
+        top = max(row.values())
+        out["saturation_E"][N] = min(E for E, g in row.items() if g >= 0.9 * top)
     return out
 
 
