@@ -62,6 +62,8 @@ def _load():
         lib.orc_deriv.restype = None
         lib.orc_nodes.argtypes = [ctypes.c_int] * 4 + [_d, _d, _d]
         lib.orc_nodes.restype = None
+        lib.orc_nodes_rel.argtypes = [ctypes.c_int] * 4 + [_d, _d, _d]
+        lib.orc_nodes_rel.restype = None
         lib.orc_geometry.argtypes = [ctypes.c_long, ctypes.c_int, _d, _d, _d, _d, _d]
         lib.orc_geometry.restype = ctypes.c_long
         lib.orc_ax_local.argtypes = [ctypes.c_long, ctypes.c_int, _d, _d, _d, _d]
@@ -127,6 +129,19 @@ def nodes(nx, ny, nz, N, verts, xi=None):
     return X
 
 
+def nodes_rel(nx, ny, nz, N, verts, xi=None):
+    """Nodal coordinates [nL, 3] relative to each element's first vertex
+    (the trilinear map of the vertex differences): the input of ``geometry``
+    for a box mesh, free of the O(1) offset's rounding."""
+    lib = _load()
+    if xi is None:
+        xi, _ = gll(N)
+    E = nx * ny * nz
+    X = np.empty((E * (N + 1) ** 3, 3))
+    lib.orc_nodes_rel(nx, ny, nz, N, _p(_f64(verts)), _p(_f64(xi)), _p(X))
+    return X
+
+
 def geometry(E, N, X, D, w):
     """Geometric factors G [nL, 6] = (rr, rs, rt, ss, st, tt) and mass B [nL]."""
     lib = _load()
@@ -175,7 +190,11 @@ class Problem:
         self.xi, self.w = gll(self.N)
         self.D = deriv(self.N, self.xi)
         self.X = nodes(self.nx, self.ny, self.nz, self.N, self.verts, self.xi)
-        self.G, self.B = geometry(self.E, self.N, self.X, self.D, self.w)
+        # J from coordinates relative to each element's first vertex (same
+        # derivative; rounding relative to the element size)
+        Xrel = nodes_rel(self.nx, self.ny, self.nz, self.N, self.verts, self.xi)
+        self.G, self.B = geometry(self.E, self.N, Xrel, self.D, self.w)
+        del Xrel
         self.gid, self.onbdry = gid(self.nx, self.ny, self.nz, self.N)
         self.nG = (self.nx * self.N + 1) * (self.ny * self.N + 1) * (self.nz * self.N + 1)
         counts = np.bincount(self.gid, minlength=self.nG)

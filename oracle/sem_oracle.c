@@ -171,6 +171,43 @@ void orc_nodes(int nx, int ny, int nz, int N, const double *verts,
     }
 }
 
+/* The same nodal coordinates, each relative to its element's first vertex: */
+/* the trilinear map applied to the vertex differences V_c - V_0.  A        */
+/* translation does not change J, and coordinates formed this way carry     */
+/* rounding relative to the element size h instead of to the O(1) position */
+/* in the cube -- which, divided by h in the derivative and amplified by   */
+/* sum_m |D_im| (~30 at N = 7), would cost ~1e-13 in G at h = 1/32.         */
+void orc_nodes_rel(int nx, int ny, int nz, int N, const double *verts,
+                   const double *xi, double *X)
+{
+    int n = N + 1;
+    for (int ez = 0; ez < nz; ++ez)
+    for (int ey = 0; ey < ny; ++ey)
+    for (int ex = 0; ex < nx; ++ex) {
+        long e = ex + (long)nx * (ey + (long)ny * ez);
+        long v0 = ex + (long)(nx + 1) * (ey + (long)(ny + 1) * ez);
+        for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            long l = i + n * (j + n * (k + (long)n * e));
+            double r = xi[i], s = xi[j], t = xi[k];
+            double hr[2] = {0.5 * (1.0 - r), 0.5 * (1.0 + r)};
+            double hs[2] = {0.5 * (1.0 - s), 0.5 * (1.0 + s)};
+            double ht[2] = {0.5 * (1.0 - t), 0.5 * (1.0 + t)};
+            for (int d = 0; d < 3; ++d) {
+                double acc = 0.0;
+                for (int c = 0; c < 2; ++c)
+                for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    long v = (ex + a) + (long)(nx + 1) * ((ey + b) + (long)(ny + 1) * (ez + c));
+                    acc += (verts[3 * v + d] - verts[3 * v0 + d]) * hr[a] * hs[b] * ht[c];
+                }
+                X[3 * l + d] = acc;
+            }
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometric factors.  J_ab = dx_a/dr_b is obtained by applying D along     */
 /* r, s, t to the nodal coordinates (exact for a trilinear map, whose degree */

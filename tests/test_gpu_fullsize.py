@@ -1,0 +1,111 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: E = 32^3 = 32768, N = 7, jitter 5 % (seed 2), the operator variants
+chosen by the per-order tuner on this problem.
+
+* FP64 geometry and operator, whole vectors, against the oracle's full
+  problem: 1e-13 relative max norm, like the small cases.
+* FP32 operator (BF16 factors) against the oracle on the same rounded
+  factors: 5e-5 relative.
+* CG: the first 5 residual norms of the full solve against the oracle's full
+  CG (rtol 1e-9); the FP64 and mixed-precision solves to 1e-8 checked with
+  the oracle's own assembled operator (true residual <= 1.5e-8).
+"""
+import numpy as np
+import pytest
+
+from paper_2606_12650_gb300.inputs import box_vertices, normal_field
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+NX, N = 32, 7
+NQ = N + 1
+NP = NQ ** 3
+
+
+def bf16_round(a):
+    m, e = np.frexp(np.asarray(a, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+@pytest.fixture(scope="module")
+def full(semlib):
+    from paper_2606_12650_gb300 import Mesh, sem
+    verts = box_vertices(NX, NX, NX, 0.05, seed=2)
+    M = Mesh(NX, NX, NX, N, verts)
+    saved = {k: sem.autotune_get(k, N) for k in (0, 2)}
+    for kind in (0, 2):                  # the bench's launch configuration
+        M.autotune(kind, reps=5)
+    yield M, verts
+    M.free()
+    for k, (v, e, _) in saved.items():
+        sem.autotune_set(k, N, v, e)
+
+
+@pytest.fixture(scope="module")
+def oracle_full(full, oracle_mod):
+    _, verts = full
+    return oracle_mod.Problem(NX, NX, NX, N, verts)
+
+
+def test_fullsize_operator(full, oracle_full, oracle_mod):
+    """Whole vectors: G, B and the FP64 operator within 1e-13 of the oracle
+    (||gpu - ref||_inf / ||ref||_inf), the FP32 operator with BF16 factors
+    within 5e-5 of the oracle on the same rounded factors."""
+    M, _ = full
+    P = oracle_full
+    x = normal_field(M.nL, 3)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    M.ax(xd, yd)
+    G = torch.empty(M.nL * 6, dtype=torch.float64, device="cuda")
+    B = torch.empty(M.nL, dtype=torch.float64, device="cuda")
+    M.geom(G, B)
+    x32 = x.astype(np.float32)
+    x32d = torch.from_numpy(x32).cuda()
+    y32d = torch.full_like(x32d, float("nan"))
+    M.ax32(x32d, y32d, 1)
+    torch.cuda.synchronize()
+
+    def rel(got, want):
+        return np.abs(got - want).max() / np.abs(want).max()
+
+    assert rel(G.cpu().numpy().reshape(-1, 6), P.G) < 1e-13
+    assert rel(B.cpu().numpy(), P.B) < 1e-13
+    del G, B
+    assert rel(yd.cpu().numpy(), P.ax_local(x)) < 1e-13
+    y32_ref = oracle_mod.ax_local(P.E, N, P.D, bf16_round(P.G), x32.astype(np.float64))
+    assert rel(y32d.cpu().numpy().astype(np.float64), y32_ref) < 5e-5
+
+
+def test_fullsize_cg_history(full, oracle_full):
+    M, _ = full
+    P = oracle_full
+    b_ref = P.mask(P.gs(normal_field(P.nL, 3)))
+    _, it_ref, h_ref = P.cg(b_ref, maxit=5, tol=0.0)
+    b = torch.from_numpy(b_ref).cuda()
+    x = torch.empty_like(b)
+    hist = torch.zeros(6, dtype=torch.float64, device="cuda")
+    it, _ = M.cg_solve(b, x, 0.0, 5, hist)
+    torch.cuda.synchronize()
+    assert it == 5 == it_ref
+    np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=0)
+
+
+def test_fullsize_solves_meet_tolerance(full, oracle_full):
+    M, _ = full
+    P = oracle_full
+    b_ref = P.mask(P.gs(normal_field(P.nL, 3)))
+    b = torch.from_numpy(b_ref).cuda()
+    x = torch.empty_like(b)
+    it, rel = M.cg_solve(b, x, 1e-8, 100000)
+    torch.cuda.synchronize()
+    assert rel <= 1e-8
+    assert P.true_residual(b_ref, x.cpu().numpy()) <= 1.5e-8
+    xm = torch.empty_like(b)
+    inner, outer, res = M.cg_mixed(b, xm, 1e-8, 50, 1e-3, 100000, 1)
+    torch.cuda.synchronize()
+    assert res <= 1e-8
+    assert P.true_residual(b_ref, xm.cpu().numpy()) <= 1.5e-8
+    assert inner <= 1.6 * it + 20
