@@ -53,14 +53,14 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
               for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
                         "sem_internal.h")]
-VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch"}
+VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch", 4: "lines_staged"}
 
 
 def kernel_label(variant, epb, N, t, gt):
     """Name of the CG-operator kernel the tuner chose."""
     q = N + 1
-    if variant in (1, 3):
-        pf = ", G prefetched" if variant == 3 else ""
+    if variant in (1, 3, 4):
+        pf = {1: "", 3: ", G prefetched", 4: ", G staged"}[variant]
         return f"ax_lines_kernel<{q},{t},{gt},CG> ({epb} elements/block{pf})"
     if variant == 2:
         return f"ax32p_kernel<{q},{gt},CG> (persistent)"

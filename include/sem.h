@@ -179,7 +179,8 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   element, FP64), 1 "lines" (whole r, s and t lines per thread with the
  *   even-odd split of D; elements per block epb chosen at launch), 2
  *   "persistent" (TMA-pipelined columns, FP32 only), 3 "lines" with the
- *   geometric factors loaded into registers ahead of use (BF16 factors only).  The variant in use is
+ *   geometric factors loaded into registers ahead of use (BF16 factors only),
+ *   4 "lines" with the factors copied into shared memory with the slab (FP32).  The variant in use is
  *   kept per kind (0 FP64, 1 FP32 with FP32 G, 2 FP32 with BF16 G) and per N;
  *   the paper's runtime specialises kernels on N and its scripts pick the
  *   thread layout (Section VIII-B); here the choice is made by timing.

@@ -128,8 +128,9 @@ int prepare_ax32(const Problem *Pb) {
 
 int launch_ax32(const Problem *Pb, const float *x, float *y, int gprec) {
     const TuneChoice c = tune_get(tune_kind_of_gprec(gprec), Pb->nq);
-    if (c.variant == kAxLines || c.variant == kAxLinesPrefetch)
-        return launch_lines32(Pb, x, y, gprec, false, c.epb, c.variant == kAxLinesPrefetch);
+    if (c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged)
+        return launch_lines32(Pb, x, y, gprec, false, c.epb,
+                              c.variant == kAxLinesPrefetch ? 1 : (c.variant == kAxLinesStaged ? 2 : 0));
     if (gprec == kGF32) {
         AxArgs<float, float> a = ax_args<float, float>(Pb, static_cast<const float *>(Pb->G32), Pb->partials, Pb->st_in);
         a.x = x;
@@ -145,8 +146,9 @@ int launch_ax32(const Problem *Pb, const float *x, float *y, int gprec) {
 
 int launch_ax32_cg(const Problem *Pb, int gprec) {
     const TuneChoice c = tune_get(tune_kind_of_gprec(gprec), Pb->nq);
-    if (c.variant == kAxLines || c.variant == kAxLinesPrefetch)
-        return launch_lines32(Pb, nullptr, nullptr, gprec, true, c.epb, c.variant == kAxLinesPrefetch);
+    if (c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged)
+        return launch_lines32(Pb, nullptr, nullptr, gprec, true, c.epb,
+                              c.variant == kAxLinesPrefetch ? 1 : (c.variant == kAxLinesStaged ? 2 : 0));
     if (gprec == kGF32) {
         AxArgs<float, float> a = ax_args<float, float>(Pb, static_cast<const float *>(Pb->G32), Pb->partials, Pb->st_in);
         a.x = Pb->r32;

@@ -25,18 +25,6 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-__device__ __forceinline__ void load_g6_smem(const __nv_bfloat16 *g, float (&v)[6]) {
-    const unsigned *q = reinterpret_cast<const unsigned *>(g);
-    const float2 a = bf16x2_to_float2(q[0]), b = bf16x2_to_float2(q[1]), c = bf16x2_to_float2(q[2]);
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
-}
-
-__device__ __forceinline__ void load_g6_smem(const float *g, float (&v)[6]) {
-    const float2 *q = reinterpret_cast<const float2 *>(g);
-    const float2 a = q[0], b = q[1], c = q[2];
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
-}
-
 template <int NQ, int EPB, typename GT>
 struct AxpShape {
     static constexpr int NQ2 = NQ * NQ;

@@ -108,6 +108,12 @@ struct LinePad {
     static constexpr int P1 = NQ == 8 ? NQ + 1 : NQ, P2 = NQ * P1, NPP = NQ * P2;
 };
 
+// Where phase 2 gets the geometric factors: loaded from global memory at use
+// (kGLoad), loaded into registers before the slab wait (kGRegs, BF16 only),
+// or copied into shared memory by the TMA engine with the slab (kGStaged,
+// FP32 arithmetic only: an element's FP64 factors would take 24 KB).
+enum LineG : int { kGLoad = 0, kGRegs = 1, kGStaged = 2 };
+
 struct LineShape {
     // values per buffer for epb elements: the larger of the staged slab
     // (+ 2 x 16 B slack for its alignment shift) and the padded U / V
@@ -119,8 +125,12 @@ struct LineShape {
         const int m = slab > pad ? slab : pad;
         return (m + vpq - 1) / vpq * vpq;
     }
-    static __host__ __device__ size_t smem(int nq, int epb, int elem_bytes) {
-        return 16 + 3 * size_t(region(nq, epb, elem_bytes)) * size_t(elem_bytes);
+    // bytes of the staged factors (g_bytes per node; 0 when not staged), + 32 B slack
+    static __host__ __device__ size_t gstage(int nq, int epb, int g_bytes) {
+        return g_bytes ? (size_t(epb) * nq * nq * nq * g_bytes + 32 + 15) / 16 * 16 : 0;
+    }
+    static __host__ __device__ size_t smem(int nq, int epb, int elem_bytes, int g_bytes = 0) {
+        return 16 + 3 * size_t(region(nq, epb, elem_bytes)) * size_t(elem_bytes) + gstage(nq, epb, g_bytes);
     }
 };
 
@@ -132,15 +142,19 @@ struct LineShape {
 // first when xs is given; *part receives this thread's <p, A_local p> partial
 // (in T).  Returns false if the slab copy timed out (status set, copies
 // drained).
-// PF (BF16 factors only): the element's geometric factors are loaded into
-// registers (3 words per node) before the slab wait, so their latency
-// overlaps the TMA copy instead of stalling phase 2.
-template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF>
+// GM (LineG): kGRegs loads the element's BF16 factors into registers (3
+// words per node) before the slab wait, kGStaged has the TMA engine copy
+// them into shared memory after the three regions, with the slab; either
+// way their latency overlaps the slab copy instead of stalling phase 2.
+template <int NQ, typename T, typename GT, bool CG, bool PRE, int GM>
 __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G, const EoMat<T> &cd,
                                             const EoMat<T> &ct, T beta, T xalpha, T *xs, const T *dinv, int64_t e0,
                                             int ne, int epb, T *regA, uint64_t *bar, uint32_t phase,
                                             int32_t *status, T *part) {
+    constexpr bool PF = GM == kGRegs;
+    constexpr bool GS = GM == kGStaged;
     static_assert(!PF || sizeof(GT) == 2, "G prefetch is for BF16 factors");
+    static_assert(!GS || sizeof(T) == 4, "G staging is for FP32 arithmetic");
     constexpr int NQ2 = NQ * NQ, NP = NQ2 * NQ;
     constexpr int P1 = LinePad<NQ>::P1, P2 = LinePad<NQ>::P2, NPP = LinePad<NQ>::NPP;
     // N+1 = 8: the staged slab's rows and columns are read in a per-thread
@@ -165,14 +179,21 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
     const SlabPlan pl1 = slab_plan(src1, bytes);
     SlabPlan pl2{0, 0, 0};
     if (CG) pl2 = slab_plan(src2, bytes);
+    // staged factors: the group's factors are one contiguous run
+    const unsigned char *gsrc = reinterpret_cast<const unsigned char *>(G + 6 * e0 * NP);
+    unsigned char *gdst = GS ? slab_dst(reinterpret_cast<unsigned char *>(regC + RG), gsrc) : nullptr;
+    SlabPlan plg{0, 0, 0};
+    if (GS) plg = slab_plan(gsrc, uint32_t(ne) * NP * 6u * uint32_t(sizeof(GT)));
     if (tid == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, pl1.mid_bytes + pl2.mid_bytes);
+        mbar_arrive_expect_tx(bar, pl1.mid_bytes + pl2.mid_bytes + plg.mid_bytes);
         slab_issue(s1, src1, pl1, bar);
         if (CG) slab_issue(s2, src2, pl2, bar);
+        if (GS) slab_issue(gdst, gsrc, plg, bar);
     }
     slab_edges(s1, src1, pl1, tid, nthreads);
     if (CG) slab_edges(s2, src2, pl2, tid, nthreads);
+    if (GS) slab_edges(gdst, gsrc, plg, tid, nthreads);
 
     const int eb = tid / NQ2;
     const int ab = tid - eb * NQ2;
@@ -269,6 +290,8 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
                 const float2 g01 = bf16x2_to_float2(gw[k][0]), g23 = bf16x2_to_float2(gw[k][1]),
                              g45 = bf16x2_to_float2(gw[k][2]);
                 g[0] = g01.x; g[1] = g01.y; g[2] = g23.x; g[3] = g23.y; g[4] = g45.x; g[5] = g45.y;
+            } else if constexpr (GS) {
+                load_g6_smem(reinterpret_cast<const GT *>(gdst) + 6 * (eb * NP + k * NQ2 + tq), g);
             } else {
                 load_g6(G, nb + k * NQ2 + tq, g);
             }
@@ -312,7 +335,7 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
     return true;
 }
 
-template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF = false>
+template <int NQ, typename T, typename GT, bool CG, bool PRE, int GM = kGLoad>
 __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -328,7 +351,7 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     const T beta = CG ? T(A.st->beta) : T(0);
     const T xalpha = CG ? T(A.st->alpha) : T(0);   // read before this launch's last block replaces it
     T part = T(0);
-    if (!lines_group<NQ, T, GT, CG, PRE, PF>(A.x, A.y, A.p, A.G, P.d, P.dt, beta, xalpha, CG ? A.xs : nullptr,
+    if (!lines_group<NQ, T, GT, CG, PRE, GM>(A.x, A.y, A.p, A.G, P.d, P.dt, beta, xalpha, CG ? A.xs : nullptr,
                                              A.dinv, e0, ne, P.epb, regA, bar, 0u, A.status, &part))
         return;
     if (CG) {
@@ -381,13 +404,13 @@ inline int line_threads(int nq, int epb) {
     return t <= 512 ? t : 0;
 }
 
-template <int NQ, typename T, typename GT, bool CG, bool PRE, bool PF>
+template <int NQ, typename T, typename GT, bool CG, bool PRE, int GM>
 static int launch_lines_nq(const Problem *Pb, const AxLineArgs<T, GT> &L) {
     const int nt = line_threads(NQ, L.epb);
     if (L.epb < 1 || nt == 0) return set_error(SEM_EARG, "ax lines: elements per block out of range");
-    const size_t sm = LineShape::smem(NQ, L.epb, int(sizeof(T)));
+    const size_t sm = LineShape::smem(NQ, L.epb, int(sizeof(T)), GM == kGStaged ? 6 * int(sizeof(GT)) : 0);
     if (sm > size_t(227) * 1024) return set_error(SEM_EARG, "ax lines: shared memory per block too large");
-    auto kern = ax_lines_kernel<NQ, T, GT, CG, PRE, PF>;
+    auto kern = ax_lines_kernel<NQ, T, GT, CG, PRE, GM>;
     // raise the dynamic shared-memory limit when a larger block is first
     // asked for (the tuner and the first solve do so before any capture)
     static size_t sm_set = 0;
@@ -404,18 +427,18 @@ static int launch_lines_nq(const Problem *Pb, const AxLineArgs<T, GT> &L) {
     return cuda_check(cudaGetLastError(), "ax_lines_kernel");
 }
 
-template <typename T, typename GT, bool CG, bool PRE = false, bool PF = false>
+template <typename T, typename GT, bool CG, bool PRE = false, int GM = kGLoad>
 static int launch_lines_any(const Problem *Pb, const AxLineArgs<T, GT> &L) {
     switch (Pb->nq) {
-        case 2: return launch_lines_nq<2, T, GT, CG, PRE, PF>(Pb, L);
-        case 3: return launch_lines_nq<3, T, GT, CG, PRE, PF>(Pb, L);
-        case 4: return launch_lines_nq<4, T, GT, CG, PRE, PF>(Pb, L);
-        case 5: return launch_lines_nq<5, T, GT, CG, PRE, PF>(Pb, L);
-        case 6: return launch_lines_nq<6, T, GT, CG, PRE, PF>(Pb, L);
-        case 7: return launch_lines_nq<7, T, GT, CG, PRE, PF>(Pb, L);
-        case 8: return launch_lines_nq<8, T, GT, CG, PRE, PF>(Pb, L);
-        case 9: return launch_lines_nq<9, T, GT, CG, PRE, PF>(Pb, L);
-        case 10: return launch_lines_nq<10, T, GT, CG, PRE, PF>(Pb, L);
+        case 2: return launch_lines_nq<2, T, GT, CG, PRE, GM>(Pb, L);
+        case 3: return launch_lines_nq<3, T, GT, CG, PRE, GM>(Pb, L);
+        case 4: return launch_lines_nq<4, T, GT, CG, PRE, GM>(Pb, L);
+        case 5: return launch_lines_nq<5, T, GT, CG, PRE, GM>(Pb, L);
+        case 6: return launch_lines_nq<6, T, GT, CG, PRE, GM>(Pb, L);
+        case 7: return launch_lines_nq<7, T, GT, CG, PRE, GM>(Pb, L);
+        case 8: return launch_lines_nq<8, T, GT, CG, PRE, GM>(Pb, L);
+        case 9: return launch_lines_nq<9, T, GT, CG, PRE, GM>(Pb, L);
+        case 10: return launch_lines_nq<10, T, GT, CG, PRE, GM>(Pb, L);
         default: return set_error(SEM_EARG, "ax lines: unsupported order");
     }
 }

@@ -6,9 +6,9 @@
 
 namespace sem {
 
-bool lines_epb_ok(int nq, int epb, size_t elem_bytes) {
+bool lines_epb_ok(int nq, int epb, size_t elem_bytes, int g_stage_bytes) {
     if (nq < 2 || nq > kMaxQ || epb < 1 || line_threads(nq, epb) == 0) return false;
-    return LineShape::smem(nq, epb, int(elem_bytes)) <= size_t(200) * 1024;
+    return LineShape::smem(nq, epb, int(elem_bytes), g_stage_bytes) <= size_t(200) * 1024;
 }
 
 int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb) {

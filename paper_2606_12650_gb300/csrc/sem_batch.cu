@@ -217,8 +217,8 @@ template <int NQ, typename T, typename GT, bool CG>
 __device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
                                               int count, T *regA, uint64_t *bar, uint32_t phase, int32_t *status,
                                               T *pt) {
-    constexpr bool PF = sizeof(GT) == 2;   // BF16 factors: prefetched into registers
-    return lines_group<NQ, T, GT, CG, false, PF>(xin, yout, pv, G, const_eo<T>(NQ, 0), const_eo<T>(NQ, 1), beta,
+    constexpr int GM = sizeof(GT) == 2 ? kGRegs : kGLoad;   // BF16 factors: prefetched into registers
+    return lines_group<NQ, T, GT, CG, false, GM>(xin, yout, pv, G, const_eo<T>(NQ, 0), const_eo<T>(NQ, 1), beta,
                                                  T(0), nullptr, nullptr, first, count, count, regA, bar, phase,
                                                  status, pt);
 }
@@ -648,7 +648,7 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         // operator body and elements per item from the tuner's table
         const int full = kBatchThreads / (P->nq * P->nq);
         const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
-        const int lines = (c.variant == kAxLines || c.variant == kAxLinesPrefetch) ? 1 : 0;
+        const int lines = (c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged) ? 1 : 0;
         const int epb = lines ? std::max(1, std::min(c.epb, full)) : full;
         q.ax_first = int(ax.size());
         for (int64_t e = 0; e < P->E; e += epb)

@@ -106,8 +106,16 @@ enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
 // of sem_ax_lines.cuh (whole lines per thread, even-odd split, elements per
 // block chosen at launch), and the persistent TMA-pipelined column kernel of
 // sem_ax32p.cuh (FP32 only), and the line kernel with the geometric factors
-// loaded into registers before the slab wait (FP32 with BF16 factors only).
-enum AxVariant : int { kAxColumns = 0, kAxLines = 1, kAxPersistent = 2, kAxLinesPrefetch = 3, kAxVariants = 4 };
+// loaded into registers before the slab wait (FP32 with BF16 factors only) or
+// staged in shared memory with the slab (FP32).
+enum AxVariant : int {
+    kAxColumns = 0,
+    kAxLines = 1,
+    kAxPersistent = 2,
+    kAxLinesPrefetch = 3,
+    kAxLinesStaged = 4,
+    kAxVariants = 5
+};
 // What is tuned: the FP64 operator, and the FP32 operator with FP32 or BF16
 // geometric factors.
 enum TuneKind : int { kTuneF64 = 0, kTuneF32G32 = 1, kTuneF32G16 = 2, kTuneKinds = 3 };
@@ -130,8 +138,9 @@ int tune_load(const char *path);
 // line-kernel launchers (sem_ax_lines64.cu, sem_ax_lines32.cu); mode 0: y = A x,
 // 1: CG operator on P's vectors, 2: Jacobi-PCG operator
 int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb);
-int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb, bool pf);
-bool lines_epb_ok(int nq, int epb, size_t elem_bytes);
+// gm: where phase 2 reads the factors (0 global, 1 registers, 2 staged in shared memory)
+int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb, int gm);
+bool lines_epb_ok(int nq, int epb, size_t elem_bytes, int g_stage_bytes = 0);
 void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 
 // ---- runtime services (sem_api.cu) ---------------------------------------

@@ -63,6 +63,8 @@ bool choice_ok(int kind, int nq, const TuneChoice &c) {
         case kAxPersistent: return kind != kTuneF64;
         case kAxLines: return lines_epb_ok(nq, c.epb, elem_bytes(kind));
         case kAxLinesPrefetch: return kind == kTuneF32G16 && lines_epb_ok(nq, c.epb, elem_bytes(kind));
+        case kAxLinesStaged:
+            return kind != kTuneF64 && lines_epb_ok(nq, c.epb, elem_bytes(kind), kind == kTuneF32G32 ? 24 : 12);
         default: return false;
     }
 }
@@ -73,14 +75,16 @@ bool choice_ok(int kind, int nq, const TuneChoice &c) {
 int candidates(int kind, int nq, TuneChoice *out, int cap) {
     int n = 0;
     out[n++] = {kind == kTuneF64 ? kAxColumns : kAxPersistent, 0, 0.0};
-    const int nv = kind == kTuneF32G16 ? 2 : 1;
+    // the line kernel, then (FP32) its variants with prefetched or staged factors
+    int variants[3] = {kAxLines, kAxLinesStaged, kAxLinesPrefetch};
+    const int nv = kind == kTuneF64 ? 1 : (kind == kTuneF32G32 ? 2 : 3);
     for (int v = 0; v < nv; ++v) {
         int prev = 0;
         for (int t : {64, 128, 192, 256, 384, 512}) {
             int epb = t / (nq * nq);
             if (epb < 1) epb = 1;
-            if (epb != prev && lines_epb_ok(nq, epb, elem_bytes(kind)) && n < cap)
-                out[n++] = {v == 0 ? kAxLines : kAxLinesPrefetch, epb, 0.0};
+            const TuneChoice c{variants[v], epb, 0.0};
+            if (epb != prev && choice_ok(kind, nq, c) && n < cap) out[n++] = c;
             prev = epb;
         }
     }
@@ -154,8 +158,8 @@ int tune_problem(Problem *P, int kind, int reps, double *cand, int cap, int *n_c
     rc = cuda_check(cudaGetLastError(), "autotune: set-up");
     if (rc != SEM_OK) return rc;
 
-    TuneChoice list[16];
-    const int n = candidates(kind, nq, list, 16);
+    TuneChoice list[24];
+    const int n = candidates(kind, nq, list, 24);
     const TuneChoice saved = tune_get(kind, nq);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     rc = cuda_check(cudaEventCreate(&e0), "autotune: event");
@@ -199,7 +203,7 @@ int tune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return set_error(SEM_EARG, std::string("autotune_save: cannot write ") + path);
     fprintf(f, "# libsem operator table: kind(0 fp64, 1 fp32/fp32 G, 2 fp32/bf16 G) N variant(0 columns, "
-               "1 lines, 2 persistent, 3 lines with G prefetch) elements_per_block us\n");
+               "1 lines, 2 persistent, 3 lines with G prefetch, 4 lines with G staged) elements_per_block us\n");
     for (int k = 0; k < kTuneKinds; ++k)
         for (int q = 2; q <= kMaxQ; ++q) {
             const TuneChoice &c = g_tab[k][q];

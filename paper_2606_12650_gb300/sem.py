@@ -297,9 +297,9 @@ def stream():
 
 # ---------------------------------------------------------------- operator tuner
 TUNE_F64, TUNE_F32_G32, TUNE_F32_G16 = 0, 1, 2           # what is tuned
-VARIANT_COLUMNS, VARIANT_LINES, VARIANT_PERSISTENT, VARIANT_LINES_PREFETCH = 0, 1, 2, 3
+VARIANT_COLUMNS, VARIANT_LINES, VARIANT_PERSISTENT, VARIANT_LINES_PREFETCH, VARIANT_LINES_STAGED = 0, 1, 2, 3, 4
 VARIANT_NAMES = {VARIANT_COLUMNS: "columns", VARIANT_LINES: "lines", VARIANT_PERSISTENT: "persistent",
-                 VARIANT_LINES_PREFETCH: "lines_prefetch"}
+                 VARIANT_LINES_PREFETCH: "lines_prefetch", VARIANT_LINES_STAGED: "lines_staged"}
 
 
 def autotune(handle: int, kind: int, reps: int = 10):

@@ -96,6 +96,8 @@ def test_autotune_table_is_checked_at_init(lib, tmp_path):
     assert "line 3" in sem.last_error()
     for entry in ("1 7 0 0",      # column kernel is FP64 only
                   "0 7 2 0",      # persistent kernel is FP32 only
+                  "0 7 4 2",      # staged factors: FP32 only
+                  "1 7 3 4",      # register prefetch: BF16 factors only
                   "0 10 1 1",     # N above 9
                   "0 0 1 1",      # N below 1
                   "0 7 1 600",    # 600 elements of 64 threads do not fit a block

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 F64, F32G32, F32G16 = 0, 1, 2
-COLUMNS, LINES, PERSISTENT, LINES_PF = 0, 1, 2, 3
+COLUMNS, LINES, PERSISTENT, LINES_PF, LINES_ST = 0, 1, 2, 3, 4
 
 
 def bf16_round(a):
@@ -121,7 +121,8 @@ def test_f32_ax_parity_every_variant(semlib, oracle_mod, N, gprec):
     kind = F32G32 if gprec == 0 else F32G16
     nq2 = (N + 1) ** 2
     epbs = sorted({1, 3, max(1, 256 // nq2), max(1, 512 // nq2)})
-    choices = [(PERSISTENT, 0)] + [(LINES, e) for e in epbs] + [(LINES_PF, e) for e in epbs if gprec == 1]
+    choices = ([(PERSISTENT, 0)] + [(LINES, e) for e in epbs] + [(LINES_ST, e) for e in epbs]
+               + [(LINES_PF, e) for e in epbs if gprec == 1])
     for v, epb in choices:
         with variant(kind, N, v, epb):
             yd = torch.full_like(xd, float("nan"))
@@ -175,8 +176,8 @@ def test_autotune_keeps_fastest_and_round_trips(semlib, oracle_mod, tmp_path):
             cands = M.autotune(kind, reps=3)
             assert len(cands) >= 3
             assert cands[0][0] == (COLUMNS if kind == F64 else PERSISTENT)
-            assert all(c[0] in ((LINES, LINES_PF) if kind == F32G16 else (LINES,)) and c[1] >= 1
-                       for c in cands[1:])
+            allowed = {F64: (LINES,), F32G32: (LINES, LINES_ST), F32G16: (LINES, LINES_ST, LINES_PF)}[kind]
+            assert all(c[0] in allowed and c[1] >= 1 for c in cands[1:])
             assert all(c[2] > 0 for c in cands)
             best = min(cands, key=lambda c: c[2])
             v, e, us = sem.autotune_get(kind, 7)
@@ -189,6 +190,8 @@ def test_autotune_keeps_fastest_and_round_trips(semlib, oracle_mod, tmp_path):
         sem.autotune_set(F32G16, 7, PERSISTENT)
         with pytest.raises(sem.SemError):        # the prefetching line kernel is for BF16 factors only
             sem.autotune_set(F32G32, 7, LINES_PF, 4)
+        with pytest.raises(sem.SemError):        # staged factors are for FP32 arithmetic only
+            sem.autotune_set(F64, 7, LINES_ST, 4)
         sem.autotune_load(str(path))
         for k in (F64, F32G32, F32G16):
             v, e, us = sem.autotune_get(k, 7)
