@@ -2,14 +2,17 @@
 // orders solved together: each CG phase is ONE persistent launch over all
 // problems, replayed from a CUDA graph.
 //
-// Work lists.  Every problem is cut into operator items (groups of elements)
-// and vector items (row-aligned runs of ~4096 local nodes).  A persistent
-// kernel's CTAs take items from a global counter (dynamic load balance across
-// problems of very different cost); a device-side switch on N dispatches to
-// the body compiled for that order.  The operator body and the elements per
-// item follow the per-order tuner's table for the batch's precision: the
-// line body (sem_ax_lines.cuh) with the tuned elements per group, capped at
-// what 256 threads hold, or the column body with 256 / (N+1)^2 elements.
+// Work lists.  Every problem is cut into operator items (~16384 local nodes:
+// several passes of a 256-thread block) and vector items (row-aligned runs of
+// ~16384 local nodes).  A persistent kernel's CTAs take items from a global
+// counter (dynamic load balance across problems of very different cost); a
+// device-side switch on N dispatches to the body compiled for that order.
+// The operator body and the elements per pass follow the per-order tuner's
+// table for the batch's precision: the line body (sem_ax_lines.cuh) with the
+// tuned elements per block, capped at what 256 threads hold, or the column
+// body with 256 / (N+1)^2 elements.  Items of problems whose solve finished
+// are dropped from the lists between rounds (their order within a problem,
+// and so its reductions, never change).
 //
 // Per-problem reductions.  Each item writes one partial (fixed-order block
 // tree) to its own slot; the problem's last item to finish (per-problem
@@ -22,7 +25,7 @@
 // (mixed precision: its inner solve ended, so the FP64 correction, residual
 // and restart run this round), `finished`.  Problems can join between rounds
 // (continuous batching); finished ones are reported through a device list and
-// their items become no-ops.  One round = the init phase for joining
+// their items leave the lists.  One round = the init phase for joining
 // problems, K CG iterations replayed from a CUDA graph, and (mixed) the
 // refinement phase for problems whose inner solve stopped -- each problem
 // refines as soon as its own inner solve ends, not in lockstep.
@@ -43,7 +46,8 @@
 namespace sem {
 
 constexpr int kBatchThreads = 256;
-constexpr int kVecItemNodes = 4096;
+constexpr int kVecItemNodes = 16384;
+constexpr int kAxItemNodes = 16384;  // local nodes per operator item (several passes of the block)
 
 struct BatchProb {
     int nq, nx, ny, nz;
@@ -71,7 +75,7 @@ struct BatchItem {
     int prob, nq;
     int64_t first;  // first element (operator) or first local node (vector)
     int count;      // elements or nodes
-    int lines;      // operator items: 1 = line body, 0 = column body
+    int group;      // operator items: elements per pass of the line body; 0 = column body
 };
 
 struct BatchQueue {
@@ -83,7 +87,8 @@ enum BatchQ : int { kQAx = 0, kQVec = 1, kNumQ = 2 };
 struct BatchCtl {
     BatchQueue q[kNumQ];
     unsigned n_finished;            // entries in the finished list
-    unsigned pad[3];
+    int n_items[kNumQ];             // items in the current (compacted) lists
+    unsigned pad;
 };
 
 struct Batch {
@@ -92,7 +97,12 @@ struct Batch {
     double tol = 1e-8, inner_tol = 1e-3;
     int maxit = 100000, max_outer = 50;
     std::vector<Problem *> probs;
-    int n_ax = 0, n_vec = 0;
+    int n_ax = 0, n_vec = 0;        // items in the device lists now
+    // every member's items as built by batch_set, with its range in them; a
+    // member whose solve finished is left out of the device lists (`gone`)
+    std::vector<BatchItem> ax_all, vec_all;
+    std::vector<int> ax_first_all, vec_first_all;
+    std::vector<uint8_t> gone;
     int cap_probs = 0, cap_ax = 0, cap_vec = 0;
     BatchProb *d_probs = nullptr;
     BatchItem *d_ax = nullptr, *d_vec = nullptr;
@@ -202,33 +212,63 @@ __device__ __forceinline__ bool item_partial(double v0, double *part, int it, ui
 }
 
 // ------------------------------------------------------------------ operator
-// One item of order NQ.  Kept out of line so that each order's body gets its
-// own register allocation (inlined into one switch, the nine bodies share and
-// exhaust the register file).
+// One item of order NQ: `count` elements from `first`, taken in groups of
+// what one pass of the block holds (`group` elements), so that an item's
+// fixed costs -- the queue ticket, the call, the block reduction of its
+// partial -- are shared by several groups.  Kept out of line so that each
+// order's body gets its own register allocation (inlined into one switch, the
+// nine bodies share and exhaust the register file).  *phase is the mbarrier
+// phase of the next completion; each group uses one.
 template <int NQ, typename T, typename GT, bool CG>
 __device__ __noinline__ bool batch_ax_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
-                                           int count, T *regA, uint64_t *bar, uint32_t phase, int32_t *status,
+                                           int count, T *regA, uint64_t *bar, uint32_t *phase, int32_t *status,
                                            T *pt) {
-    return ax_group<NQ, BEpb<NQ>::value, T, GT, CG>(xin, yout, pv, G, ConstD<NQ, T>{}, beta, first, count, regA,
-                                                   bar, phase, status, pt);
+    constexpr int GR = BEpb<NQ>::value;
+    T acc = T(0);
+    for (int g = 0; g < count; g += GR) {
+        T part = T(0);
+        const bool ok = ax_group<NQ, GR, T, GT, CG>(xin, yout, pv, G, ConstD<NQ, T>{}, beta, first + g,
+                                                    min(GR, count - g), regA, bar, *phase, status, &part);
+        *phase ^= 1u;
+        if (!ok) return false;
+        acc += part;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    *pt = acc;
+    return true;
 }
 
 template <int NQ, typename T, typename GT, bool CG>
 __device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
-                                              int count, T *regA, uint64_t *bar, uint32_t phase, int32_t *status,
-                                              T *pt) {
-    constexpr int GM = sizeof(GT) == 2 ? kGRegs : kGLoad;   // BF16 factors: prefetched into registers
-    return lines_group<NQ, T, GT, CG, false, GM>(xin, yout, pv, G, const_eo<T>(NQ, 0), const_eo<T>(NQ, 1), beta,
-                                                 T(0), nullptr, nullptr, first, count, count, regA, bar, phase,
-                                                 status, pt);
+                                              int count, int group, T *regA, uint64_t *bar, uint32_t *phase,
+                                              int32_t *status, T *pt) {
+    constexpr int GM = kGLoad;   // factors loaded at use: the register prefetch would not fit 4 CTAs per SM
+    T acc = T(0);
+    for (int g = 0; g < count; g += group) {
+        T part = T(0);
+        const bool ok = lines_group<NQ, T, GT, CG, false, GM>(xin, yout, pv, G, const_eo<T>(NQ, 0),
+                                                              const_eo<T>(NQ, 1), beta, T(0), nullptr, nullptr,
+                                                              first + g, min(group, count - g), group, regA, bar,
+                                                              *phase, status, &part);
+        *phase ^= 1u;
+        if (!ok) return false;
+        acc += part;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    *pt = acc;
+    return true;
 }
 
 // mode: 0 = FP64 CG (p = r + beta p, w = A p), 1 = FP64 plain (w = A x),
 //       2 = FP32 inner CG on the FP32 vectors
+// FP32 items are HBM-bound: 4 CTAs per SM (<= 64 registers) for latency
+// hiding; FP64 items are FP64-pipe bound and keep the column body's registers.
 template <typename T, typename GT, int MODE>
-__global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *probs, const BatchItem *items,
-                                                                 int nitems, double *part, uint32_t *tickets,
-                                                                 BatchCtl *ctl, int32_t *status) {
+__global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2) batch_ax_kernel(BatchProb *probs, const BatchItem *items,
+                                                                 double *part, uint32_t *tickets, BatchCtl *ctl,
+                                                                 int32_t *status) {
     constexpr bool CG = MODE != 1;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
@@ -239,6 +279,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
     __syncthreads();
     uint32_t phase = 0;
     BatchQueue *q = &ctl->q[kQAx];
+    const int nitems = ctl->n_items[kQAx];
     while (true) {
         const int it = next_item(q, &s_item);
         if (it >= nitems) break;
@@ -255,20 +296,19 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_ax_kernel(BatchProb *p
         else { xin = reinterpret_cast<const T *>(P.r32); yout = reinterpret_cast<T *>(P.w32); pv = reinterpret_cast<T *>(P.p32); }
         const GT *G = prob_G<GT>(P);
         T pt = T(0);
-        bool ok = true, used = true;
+        bool ok = true;
         switch (item.nq) {
-#define SEM_BAX(Q)                                                                                     \
-    case Q:                                                                                            \
-        ok = item.lines ? batch_lines_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count, \
-                                                         regA, bar, phase, status, &pt)                  \
-                        : batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,    \
-                                                      regA, bar, phase, status, &pt);                    \
+#define SEM_BAX(Q)                                                                                       \
+    case Q:                                                                                              \
+        ok = item.group ? batch_lines_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,   \
+                                                         item.group, regA, bar, &phase, status, &pt)       \
+                        : batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,      \
+                                                      regA, bar, &phase, status, &pt);                     \
         break;
             SEM_BAX(2) SEM_BAX(3) SEM_BAX(4) SEM_BAX(5) SEM_BAX(6) SEM_BAX(7) SEM_BAX(8) SEM_BAX(9) SEM_BAX(10)
 #undef SEM_BAX
-            default: used = false; break;
+            default: break;
         }
-        if (used) phase ^= 1u;
         if (!ok) return;  // timed out: the status word reports it; the solve is abandoned
         if (CG) {
             const double bs = block_sum(double(pt), red);
@@ -401,14 +441,14 @@ __device__ __forceinline__ void init_state(CgState *st, double rho0, double tol,
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBatchThreads, 3) batch_vec_kernel(BatchProb *probs, const BatchItem *items,
-                                                                  int nitems, double *part, uint32_t *tickets,
-                                                                  BatchCtl *ctl, int32_t *finished_ids,
-                                                                  VecArgs A) {
+__global__ void __launch_bounds__(kBatchThreads, MODE == kVecUpdate32 ? 4 : 3) batch_vec_kernel(BatchProb *probs, const BatchItem *items,
+                                                                  double *part, uint32_t *tickets, BatchCtl *ctl,
+                                                                  int32_t *finished_ids, VecArgs A) {
     __shared__ double red[32];
     __shared__ int s_item;
     constexpr bool REDUCES = MODE != kVecCorrect;
     BatchQueue *q = &ctl->q[kQVec];
+    const int nitems = ctl->n_items[kQVec];
     while (true) {
         const int it = next_item(q, &s_item);
         if (it >= nitems) break;
@@ -493,8 +533,8 @@ template <typename T, typename GT, int MODE>
 static int launch_bax(Batch *B, int grid) {
     const size_t sm = batch_ax_smem<T>();
     const int g = std::max(1, std::min(grid, B->n_ax));
-    batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(
-        B->d_probs, B->d_ax, B->n_ax, B->part, B->tickets, B->ctl, status_word());
+    batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(B->d_probs, B->d_ax, B->part,
+                                                                             B->tickets, B->ctl, status_word());
     count_launches(1);
     return cuda_check(cudaGetLastError(), "batch_ax_kernel");
 }
@@ -503,8 +543,8 @@ template <int MODE>
 static int launch_bvec(Batch *B) {
     const VecArgs A{B->mode, B->maxit, B->max_outer, 0, B->tol, B->inner_tol};
     const int g = std::max(1, std::min(B->grid_vec, B->n_vec));
-    batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->n_vec, B->part,
-                                                                       B->tickets, B->ctl, B->finished_ids, A);
+    batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->part, B->tickets,
+                                                                       B->ctl, B->finished_ids, A);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "batch_vec_kernel");
 }
@@ -588,6 +628,71 @@ static int read_ctl(Batch *B) {
     return rc;
 }
 
+// New item ranges of the members after a compaction (ax_first, ax_count,
+// vec_first, vec_count per member; a finished member gets empty ranges).
+__global__ void batch_relist_kernel(BatchProb *probs, const int4 *ranges, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int4 r = ranges[k];
+    probs[k].ax_first = r.x;
+    probs[k].ax_count = r.y;
+    probs[k].vec_first = r.z;
+    probs[k].vec_count = r.w;
+}
+
+// Device item lists with the items of the members still solving, in member
+// order (a member's items keep their order, so its reductions -- partials in
+// its item order -- are unchanged and its iterates stay bit-identical).
+// Finished members' items would otherwise each cost a queue ticket and a
+// state read per launch for the rest of the solve.
+static int compact(Batch *B) {
+    const int n = int(B->probs.size());
+    std::vector<BatchItem> ax, vec;
+    std::vector<int4> ranges(n);
+    for (int k = 0; k < n; ++k) {
+        const Problem *P = B->probs[k];
+        (void)P;
+        const int a0 = B->ax_first_all[k], a1 = B->ax_first_all[k + 1];
+        const int v0 = B->vec_first_all[k], v1 = B->vec_first_all[k + 1];
+        if (B->gone[k]) {
+            ranges[k] = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        ranges[k] = make_int4(int(ax.size()), a1 - a0, int(vec.size()), v1 - v0);
+        ax.insert(ax.end(), B->ax_all.begin() + a0, B->ax_all.begin() + a1);
+        vec.insert(vec.end(), B->vec_all.begin() + v0, B->vec_all.begin() + v1);
+    }
+    int rc = SEM_OK;
+    int4 *d_ranges = static_cast<int4 *>(dev_alloc(sizeof(int4) * size_t(std::max(n, 1))));
+    if (!d_ranges) return SEM_ENOMEM;
+    rc = cuda_check(cudaMemcpyAsync(d_ranges, ranges.data(), sizeof(int4) * size_t(n), cudaMemcpyHostToDevice,
+                                    stream()), "batch: ranges");
+    if (rc == SEM_OK) {
+        batch_relist_kernel<<<unsigned((n + 127) / 128), 128, 0, stream()>>>(B->d_probs, d_ranges, n);
+        count_launches(1);
+        rc = cuda_check(cudaGetLastError(), "batch_relist_kernel");
+    }
+    if (rc == SEM_OK && !ax.empty())
+        rc = cuda_check(cudaMemcpyAsync(B->d_ax, ax.data(), sizeof(BatchItem) * ax.size(), cudaMemcpyHostToDevice,
+                                        stream()), "batch: items");
+    if (rc == SEM_OK && !vec.empty())
+        rc = cuda_check(cudaMemcpyAsync(B->d_vec, vec.data(), sizeof(BatchItem) * vec.size(), cudaMemcpyHostToDevice,
+                                        stream()), "batch: items");
+    const int counts[kNumQ] = {int(ax.size()), int(vec.size())};
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(B->ctl->n_items, counts, sizeof counts, cudaMemcpyHostToDevice, stream()),
+                        "batch: item counts");
+    // the host copies above come from pageable memory; finish them before
+    // the vectors go out of scope
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
+    dev_free(d_ranges);
+    if (rc == SEM_OK) {
+        B->n_ax = counts[0];
+        B->n_vec = counts[1];
+    }
+    return rc;
+}
+
 Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_outer, int K) {
     Batch *B = new Batch();
     B->mode = mode;
@@ -645,14 +750,17 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
             q.outer_done = 0;
             any_init = true;
         }
-        // operator body and elements per item from the tuner's table
+        // operator body and elements per pass from the tuner's table; an item
+        // holds several passes (~kAxItemNodes local nodes)
         const int full = kBatchThreads / (P->nq * P->nq);
         const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
-        const int lines = (c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged) ? 1 : 0;
-        const int epb = lines ? std::max(1, std::min(c.epb, full)) : full;
+        const bool lines = c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged;
+        const int group = lines ? std::max(1, std::min(c.epb, full)) : full;
+        const int np = P->nq * P->nq * P->nq;
+        const int per_item = group * std::max(1, kAxItemNodes / (np * group));
         q.ax_first = int(ax.size());
-        for (int64_t e = 0; e < P->E; e += epb)
-            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(epb, P->E - e)), lines});
+        for (int64_t e = 0; e < P->E; e += per_item)
+            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(per_item, P->E - e)), lines ? group : 0});
         q.ax_count = int(ax.size()) - q.ax_first;
         const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
         q.vec_first = int(vec.size());
@@ -679,6 +787,17 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     B->probs.assign(probs, probs + n);
     B->n_ax = int(ax.size());
     B->n_vec = int(vec.size());
+    B->ax_all = ax;
+    B->vec_all = vec;
+    B->ax_first_all.assign(n + 1, 0);
+    B->vec_first_all.assign(n + 1, 0);
+    for (int k = 0; k < n; ++k) {
+        B->ax_first_all[k] = hp[k].ax_first;
+        B->vec_first_all[k] = hp[k].vec_first;
+    }
+    B->ax_first_all[n] = B->n_ax;
+    B->vec_first_all[n] = B->n_vec;
+    B->gone.assign(n, 0);
     B->any_init = any_init;
     if (n)
         rc = cuda_check(cudaMemcpyAsync(B->d_probs, hp.data(), sizeof(BatchProb) * n, cudaMemcpyHostToDevice,
@@ -693,6 +812,11 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         rc = cuda_check(cudaMemsetAsync(B->tickets, 0, sizeof(uint32_t) * 2 * size_t(B->cap_probs), stream()), "batch");
     // the finished list restarts with the new membership
     if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(&B->ctl->n_finished, 0, sizeof(unsigned), stream()), "batch");
+    const int counts[kNumQ] = {B->n_ax, B->n_vec};
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(B->ctl->n_items, counts, sizeof counts, cudaMemcpyHostToDevice, stream()),
+                        "batch: item counts");
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
     B->seen_finished = 0;
     if (B->graph) {
         cudaGraphExecDestroy(B->graph);
@@ -783,8 +907,13 @@ int batch_round(Batch *B, std::vector<int> *done) {
                                         cudaMemcpyDeviceToHost, stream()), "batch: finished list");
         if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
         if (rc != SEM_OK) return rc;
-        for (int32_t k : ids) done->push_back(k);
+        for (int32_t k : ids) {
+            done->push_back(k);
+            if (k >= 0 && k < int(B->gone.size())) B->gone[k] = 1;
+        }
         B->seen_finished = nf;
+        rc = compact(B);
+        if (rc != SEM_OK) return rc;
     }
     return SEM_OK;
 }
