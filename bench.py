@@ -53,6 +53,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
               for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
                         "sem_internal.h")]
+AX32_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
+                for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax32.cu", "sem_ax_lines32.cu", "sem_ax32p.cuh",
+                          "sem_device.cuh", "sem_internal.h")]
 VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch", 4: "lines_staged"}
 
 
@@ -460,6 +463,14 @@ def run_mixed(a, M, b, x64, t64_ms, job, stream, sem, torch):
     alg = E * (N + 1) ** 3 * 28   # r, p in (FP32); p, w out (FP32); 6 BF16 factors
     peak, how = hbm_peak()
     gbs = alg / (ax_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh).get("ax_f32_bf16_cg", {})
+        if t.get("source_sha") == source_sha(AX32_SOURCES) and t.get("E") == E and t.get("N") == N:
+            traffic = t.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
     # 1e-10: FP64 CG reference and mixed refinement
     x10 = torch.empty_like(b)
     t0 = time.perf_counter()
@@ -480,7 +491,7 @@ def run_mixed(a, M, b, x64, t64_ms, job, stream, sem, torch):
             "inner_iters_per_solve": inner_tot // max(a.steps, 1), "outer_iters": outer,
             "rel_res_true": true_res, "err_vs_fp64_cg_inf": err_vs_fp64,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "traffic": None,
+                         "traffic": traffic,
                          "kernel": kernel_label(*sem.autotune_get(sem.TUNE_F32_G16, N)[:2], N, "float", "bf16"),
                          "launch_ms": ax_ms, "alg_bytes_per_launch": alg, "peak_source": how},
             "tol_1e-10": {"fp64_cg_iters": it10, "fp64_ms": 1e3 * t_fp64_10,
