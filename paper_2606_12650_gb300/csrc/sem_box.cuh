@@ -133,6 +133,15 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
     const bool has_hi = i0 + V - 1 == N && ex < nx - 1;   // node i = N has a higher r neighbour
     const bool mask_lo = i0 == 0 && ex == 0;
     const bool mask_hi = i0 + V - 1 == N && ex == nx - 1;
+    // the node's own values first: their loads then overlap those of w and
+    // its neighbour copies below instead of waiting for the sum
+    T xv[V], pv[V], rv[V], dv[V];
+    if (!DX) {
+        vload<T, V>(x + l0, xv);
+        vload<T, V>(p + l0, pv);
+    }
+    vload<T, V>(r + l0, rv);
+    if (PRE) vload<T, V>(dinv + l0, dv);
     T sv[V];
     if (sy == 0 && sz == 0) {
         // Row inside the element in s and t: copies only across the r faces.
@@ -193,13 +202,6 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
             sv[v] = s;
         }
     }
-    T xv[V], pv[V], rv[V], dv[V];
-    if (!DX) {
-        vload<T, V>(x + l0, xv);
-        vload<T, V>(p + l0, pv);
-    }
-    vload<T, V>(r + l0, rv);
-    if (PRE) vload<T, V>(dinv + l0, dv);
     const bool owner_row = sy >= 0 && sz >= 0;
     Acc rr = Acc(0);
 #pragma unroll
