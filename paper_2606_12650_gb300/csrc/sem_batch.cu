@@ -51,6 +51,7 @@ constexpr int kAxItemNodes = 16384;  // local nodes per operator item (several p
 
 struct BatchProb {
     int nq, nx, ny, nz;
+    BoxDims bd;                     // the box with its fast divisors
     int64_t E, nL;
     const double *G;
     const __nv_bfloat16 *G16;
@@ -379,6 +380,7 @@ __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, int64_t 
     if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
         using T = typename std::conditional<MODE == kVecUpdate64, double, float>::type;
         constexpr int V = UpdVec<NQ, T>::value;
+        const BoxDims bd = P.bd;   // in registers for the whole item
         T *x = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.x) : reinterpret_cast<T *>(P.d32);
         T *r = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.r) : reinterpret_cast<T *>(P.r32);
         const T *p = MODE == kVecUpdate64 ? reinterpret_cast<const T *>(P.p) : reinterpret_cast<const T *>(P.p32);
@@ -386,7 +388,7 @@ __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, int64_t 
         const T alpha = T(st->alpha);
         T a = T(0);
         for (int v = tid; v < count / V; v += blockDim.x)
-            update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, P.nx, P.ny, P.nz, alpha, a);
+            update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, bd, alpha, a);
         acc = double(a);
     } else if (MODE == kVecInit64) {
         // <b, b> over global nodes (each counted at its first copy)
@@ -539,10 +541,26 @@ static int launch_bax(Batch *B, int grid) {
     return cuda_check(cudaGetLastError(), "batch_ax_kernel");
 }
 
+// Resident CTAs of one vector phase's kernel (the phases differ in
+// registers); computed once, before any capture (batch_attrs).
+template <int MODE>
+static int vec_grid(int *out) {
+    static int grid = 0;
+    if (!grid) {
+        const int rc = batch_grid(reinterpret_cast<const void *>(batch_vec_kernel<MODE>), 0, &grid);
+        if (rc != SEM_OK) return rc;
+    }
+    *out = grid;
+    return SEM_OK;
+}
+
 template <int MODE>
 static int launch_bvec(Batch *B) {
     const VecArgs A{B->mode, B->maxit, B->max_outer, 0, B->tol, B->inner_tol};
-    const int g = std::max(1, std::min(B->grid_vec, B->n_vec));
+    int grid = 0;
+    const int rcg = vec_grid<MODE>(&grid);
+    if (rcg != SEM_OK) return rcg;
+    const int g = std::max(1, std::min(grid, B->n_vec));
     batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->part, B->tickets,
                                                                        B->ctl, B->finished_ids, A);
     count_launches(1);
@@ -605,6 +623,13 @@ static int batch_attrs(Batch *B) {
                         batch_ax_smem<float>(), &B->grid_ax32);
     if (rc == SEM_OK)
         rc = batch_grid(reinterpret_cast<const void *>(batch_vec_kernel<kVecUpdate64>), 0, &B->grid_vec);
+    int g = 0;
+    if (rc == SEM_OK) rc = vec_grid<kVecUpdate64>(&g);
+    if (rc == SEM_OK) rc = vec_grid<kVecUpdate32>(&g);
+    if (rc == SEM_OK) rc = vec_grid<kVecInit64>(&g);
+    if (rc == SEM_OK) rc = vec_grid<kVecInner>(&g);
+    if (rc == SEM_OK) rc = vec_grid<kVecCorrect>(&g);
+    if (rc == SEM_OK) rc = vec_grid<kVecResidual>(&g);
     return rc;
 }
 
@@ -737,6 +762,7 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         for (size_t j = 0; j < B->probs.size(); ++j)
             if (B->probs[j] == P) q = old[j];       // keep the solve state
         q.nq = P->nq; q.nx = P->nx; q.ny = P->ny; q.nz = P->nz;
+        q.bd = box_dims(P->nx, P->ny, P->nz);
         q.E = P->E; q.nL = P->nL;
         q.G = P->G; q.G16 = static_cast<const __nv_bfloat16 *>(P->G16); q.G32 = static_cast<const float *>(P->G32);
         q.x = P->x; q.r = P->r; q.p = P->p; q.w = P->w;

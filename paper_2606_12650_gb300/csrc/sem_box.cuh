@@ -26,6 +26,33 @@ struct BoxNode {
     bool owner;         // first copy of its global node
 };
 
+// Division by a divisor d >= 1 fixed for a launch, for dividends n < 2^31:
+// with l = ceil(log2 d) and m = ceil(2^(31+l) / d) < 2^32, floor(n / d) =
+// floor(n m / 2^(31+l)) (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994, Thm 4.2 with N = 31).  One wide
+// multiply and a shift instead of the ~20-instruction integer division.
+struct DivU {
+    uint32_t m;
+    uint32_t s;
+};
+
+inline DivU make_divu(uint32_t d) {
+    uint32_t l = 0;
+    while ((uint64_t(1) << l) < d) ++l;
+    const uint64_t m = ((uint64_t(1) << (31 + l)) + d - 1) / d;
+    return DivU{uint32_t(m), 31 + l};
+}
+
+__device__ __forceinline__ uint32_t divu(uint32_t n, DivU D) { return uint32_t((uint64_t(n) * D.m) >> D.s); }
+
+// Box sizes with their fast divisors (element index -> (ex, ey, ez)).
+struct BoxDims {
+    int nx, ny, nz;
+    DivU dx, dy;
+};
+
+inline BoxDims box_dims(int nx, int ny, int nz) { return BoxDims{nx, ny, nz, make_divu(uint32_t(nx)), make_divu(uint32_t(ny))}; }
+
 template <int NQ>
 __device__ __forceinline__ BoxNode box_node(int l, int nx, int ny, int nz) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
@@ -112,16 +139,17 @@ __device__ __forceinline__ void vstore(T *p, const T (&v)[V]) {
 // node's first copy.
 template <int NQ, int V, typename T, typename Acc, bool PRE = false, bool DX = false>
 __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                          const T *__restrict__ w, int l0, int nx, int ny, int nz, T alpha,
+                                          const T *__restrict__ w, int l0, const BoxDims &bd, T alpha,
                                           Acc &acc, const T *__restrict__ dinv = nullptr,
                                           Acc *acc_rr = nullptr) {
     constexpr int N = NQ - 1, NQ2 = NQ * NQ, NP = NQ2 * NQ;
+    const int nx = bd.nx, ny = bd.ny, nz = bd.nz;
     const unsigned e = unsigned(l0) / unsigned(NP);
     const int q = l0 - int(e) * NP;
     const int i0 = q % NQ, j = (q / NQ) % NQ, k = q / NQ2;
-    const unsigned t = e / unsigned(nx);
+    const unsigned t = divu(e, bd.dx);
     const int ex = int(e - t * unsigned(nx));
-    const unsigned tz = t / unsigned(ny);
+    const unsigned tz = divu(t, bd.dy);
     const int ey = int(t - tz * unsigned(ny)), ez = int(tz);
     const int sy = j == 0 ? -1 : (j == N ? 1 : 0);
     const int sz = k == 0 ? -1 : (k == N ? 1 : 0);
@@ -280,8 +308,7 @@ __global__ void assemble_box_kernel(const double *__restrict__ f, double *__rest
 template <int NQ, typename T, typename Acc>
 __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x, T *__restrict__ r,
                                                               const T *__restrict__ p, const T *__restrict__ w,
-                                                              int nL, int nx, int ny, int nz, double *partials,
-                                                              CgState *st) {
+                                                              int nL, BoxDims bd, double *partials, CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     const T alpha = T(st->alpha);
@@ -289,7 +316,7 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
     constexpr int V = UpdVec<NQ, T>::value;
     const int nv = nL / V;   // nL is a multiple of (N+1), hence of V
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nv; u += gridDim.x * blockDim.x)
-        update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, nx, ny, nz, alpha, acc);
+        update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, bd, alpha, acc);
     const double bs = block_sum(double(acc), red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
@@ -302,8 +329,7 @@ __global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x,
 template <int NQ, typename T, typename Acc>
 __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x, T *__restrict__ r,
                                                               const T *__restrict__ p, const T *__restrict__ w,
-                                                              int nL, int nx, int ny, int nz, double *partials,
-                                                              CgState *st) {
+                                                              int nL, BoxDims bd, double *partials, CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     constexpr int V = UpdVec<NQ, T>::value;
@@ -316,7 +342,7 @@ __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x,
     Acc acc = Acc(0);
     for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
         const int l0 = RM::l0(task, lane, E);
-        if (l0 >= 0) update_vec<NQ, V, T, Acc, false, true>(x, r, p, w, l0, nx, ny, nz, alpha, acc);
+        if (l0 >= 0) update_vec<NQ, V, T, Acc, false, true>(x, r, p, w, l0, bd, alpha, acc);
     }
     const double bs = block_sum(double(acc), red);
     if (publish_partial(bs, partials, &st->ticket_up)) {
@@ -351,14 +377,14 @@ static int launch_update_rows_nq(const Problem *P, T *x, T *r, const T *p, const
         int64_t blocks = (int64_t(RM::tasks(int(P->E))) * 32 + 255) / 256;
         blocks = std::min<int64_t>(blocks, int64_t(sm_count()) * 8);
         cg_update_class_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(
-            x, r, p, w, int(P->nL), P->nx, P->ny, P->nz, P->partials, st);
+            x, r, p, w, int(P->nL), box_dims(P->nx, P->ny, P->nz), P->partials, st);
         count_launches(1);
         return cuda_check(cudaGetLastError(), "cg_update_class_kernel");
     }
     int64_t blocks = (P->nL / V + 255) / 256;
     blocks = std::min(blocks, resident_blocks(cg_update_nodes_kernel<NQ, T, Acc>, 256));
-    cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(x, r, p, w, int(P->nL), P->nx,
-                                                                               P->ny, P->nz, P->partials, st);
+    cg_update_nodes_kernel<NQ, T, Acc><<<unsigned(blocks), 256, 0, stream()>>>(
+        x, r, p, w, int(P->nL), box_dims(P->nx, P->ny, P->nz), P->partials, st);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "cg_update_nodes_kernel");
 }

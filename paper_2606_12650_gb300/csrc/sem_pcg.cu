@@ -121,8 +121,8 @@ template <int NQ>
 __global__ void __launch_bounds__(256) pcg_update_kernel(double *__restrict__ x, double *__restrict__ r,
                                                          const double *__restrict__ p,
                                                          const double *__restrict__ w,
-                                                         const double *__restrict__ dinv, int nL, int nx, int ny,
-                                                         int nz, double *partials, CgState *st) {
+                                                         const double *__restrict__ dinv, int nL, BoxDims bd,
+                                                         double *partials, CgState *st) {
     __shared__ double red[32];
     if (st->done) return;
     constexpr int V = UpdVec<NQ, double>::value;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) pcg_update_kernel(double *__restrict__ x,
     const int nwarps = int(gridDim.x * blockDim.x) >> 5;
     for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
         const int l0 = RM::l0(task, lane, E);
-        if (l0 >= 0) update_vec<NQ, V, double, double, true, true>(x, r, p, w, l0, nx, ny, nz, alpha, rz, dinv, &rr);
+        if (l0 >= 0) update_vec<NQ, V, double, double, true, true>(x, r, p, w, l0, bd, alpha, rz, dinv, &rr);
     }
     const double s0 = block_sum(rz, red);
     const double s1 = block_sum(rr, red);
@@ -152,7 +152,7 @@ static int launch_pcg_update_nq(const Problem *P) {
     int64_t blocks = (int64_t(RowMap<NQ, V>::tasks(int(P->E))) * 32 + 255) / 256;
     blocks = std::min<int64_t>(blocks, int64_t(sm_count()) * 8);
     pcg_update_kernel<NQ><<<unsigned(blocks), 256, 0, stream()>>>(P->x, P->r, P->p, P->w, P->dinv, int(P->nL),
-                                                                  P->nx, P->ny, P->nz, P->partials, P->st);
+                                                                  box_dims(P->nx, P->ny, P->nz), P->partials, P->st);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "pcg_update_kernel");
 }
