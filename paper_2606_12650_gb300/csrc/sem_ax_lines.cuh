@@ -130,7 +130,10 @@ struct LineShape {
         return g_bytes ? (size_t(epb) * nq * nq * nq * g_bytes + 32 + 15) / 16 * 16 : 0;
     }
     static __host__ __device__ size_t smem(int nq, int epb, int elem_bytes, int g_bytes = 0) {
-        return 16 + 3 * size_t(region(nq, epb, elem_bytes)) * size_t(elem_bytes) + gstage(nq, epb, g_bytes);
+        const size_t regions = 3 * size_t(region(nq, epb, elem_bytes)) * size_t(elem_bytes);
+        // the regions also hold one double per thread for the block's final sum
+        const size_t sums = size_t((epb * nq * nq + 31) / 32 * 32) * sizeof(double);
+        return 16 + (regions > sums ? regions : sums) + gstage(nq, epb, g_bytes);
     }
 };
 
@@ -349,14 +352,16 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     const T beta = CG ? T(A.st->beta) : T(0);
-    const T xalpha = CG ? T(A.st->alpha) : T(0);   // read before this launch's last block replaces it
+    // read before this launch's last block replaces it; only with a deferred x update
+    const T xalpha = (CG && A.xs) ? T(A.st->alpha) : T(0);
     T part = T(0);
     if (!lines_group<NQ, T, GT, CG, PRE, GM>(A.x, A.y, A.p, A.G, P.d, P.dt, beta, xalpha, CG ? A.xs : nullptr,
                                              A.dinv, e0, ne, P.epb, regA, bar, 0u, A.status, &part))
         return;
     if (CG) {
         // the thread's partial is formed in T; the block and grid sums are FP64
-        const double bs = block_sum(double(part), red);
+        // (the slab regions are free now and hold the block's partials)
+        const double bs = block_sum_wide(double(part), reinterpret_cast<double *>(regA));
         if (publish_partial(bs, A.partials, &A.st->ticket_ax)) {
             const double pap = finish_partials(A.partials, int(gridDim.x), &A.st->ticket_ax, red);
             if (threadIdx.x == 0) {

@@ -146,6 +146,26 @@ __device__ __forceinline__ double block_sum(double v, double *sbuf /* >= 32 */) 
     return v;
 }
 
+// Deterministic block sum with few FP64 operations: every thread's value
+// goes to shared memory, one warp adds them in a fixed order (strided per
+// lane, then a shuffle tree).  scratch: >= blockDim.x doubles of shared
+// memory that no thread still uses (the call begins with a barrier).  For
+// kernels whose other arithmetic is FP32, where the per-warp shuffle tree of
+// block_sum would keep the FP64 pipe (1/64 of the FP32 rate on GB300) busy
+// at every block's end.  Result in thread 0.
+__device__ __forceinline__ double block_sum_wide(double v, double *scratch) {
+    __syncthreads();
+    scratch[threadIdx.x] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        for (int q = threadIdx.x; q < blockDim.x; q += 32) s += scratch[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
 // Publish this block's partial and find out whether it is the last block to
 // do so.  Thread 0 writes partials[blockIdx.x]; all threads get the answer.
 __device__ __forceinline__ bool publish_partial(double v0, double *partials, uint32_t *ticket) {
