@@ -110,6 +110,46 @@ void dev_free(void *p) {
     if (g.free_fn) g.free_fn(p, g.alloc_ctx); else cudaFree(p);
 }
 
+// Pinned host slots for the small device-state mirrors that solves read back
+// once per graph replay (one CgState each).  Taken from chunks of pinned
+// memory kept for the life of the context: a solve server creates and frees
+// problems continually, and cudaMallocHost / cudaFreeHost per problem cost
+// milliseconds (the free waits for the device).
+namespace {
+constexpr size_t kPinnedSlot = 256;           // bytes per slot (>= sizeof(CgState), aligned)
+constexpr size_t kPinnedChunkSlots = 1024;
+std::vector<void *> g_pinned_chunks;
+std::vector<void *> g_pinned_free;
+}  // namespace
+
+void *pinned_slot_alloc() {
+    static_assert(sizeof(CgState) <= kPinnedSlot, "pinned slot too small");
+    if (g_pinned_free.empty()) {
+        void *chunk = nullptr;
+        if (cudaMallocHost(&chunk, kPinnedSlot * kPinnedChunkSlots) != cudaSuccess) {
+            cudaGetLastError();
+            set_error(SEM_ENOMEM, "pinned host allocation failed");
+            return nullptr;
+        }
+        g_pinned_chunks.push_back(chunk);
+        for (size_t k = kPinnedChunkSlots; k-- > 0;)
+            g_pinned_free.push_back(static_cast<unsigned char *>(chunk) + k * kPinnedSlot);
+    }
+    void *p = g_pinned_free.back();
+    g_pinned_free.pop_back();
+    return p;
+}
+
+void pinned_slot_free(void *p) {
+    if (p) g_pinned_free.push_back(p);
+}
+
+static void pinned_release_all() {
+    for (void *c : g_pinned_chunks) cudaFreeHost(c);
+    g_pinned_chunks.clear();
+    g_pinned_free.clear();
+}
+
 cudaStream_t stream() { return g.cur_stream; }
 int sm_count() { return g.prop.multiProcessorCount > 0 ? g.prop.multiProcessorCount : 1; }
 int32_t *status_word() { return g.status_dev; }
@@ -1017,6 +1057,7 @@ int sem_finalize(void) {
     dev_free(g.status_dev);
     g.status_dev = nullptr;
     if (g.status_pinned) cudaFreeHost(g.status_pinned);
+    pinned_release_all();
     g.status_pinned = nullptr;
     if (g.own_stream) cudaStreamDestroy(g.own_stream);
     g.own_stream = nullptr;

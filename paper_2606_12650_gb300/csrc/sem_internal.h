@@ -147,6 +147,8 @@ void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
 void dev_free(void *p);
 cudaStream_t stream();
+void *pinned_slot_alloc();                   // 256 pinned host bytes (CgState mirror); nullptr + error
+void pinned_slot_free(void *p);
 int sm_count();                    // SMs of the current device
 int32_t *status_word();            // device status word (kernels write it)
 int32_t *status_host();            // pinned host copy (filled by poll_status / cg_solve)

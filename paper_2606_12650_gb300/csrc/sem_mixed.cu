@@ -87,7 +87,8 @@ int mixed_prepare(Problem *P, int gprec) {
         P->w32 = static_cast<float *>(dev_alloc(vb));
         P->st_in = static_cast<CgState *>(dev_alloc(sizeof(CgState)));
         if (!P->d32 || !P->r32 || !P->p32 || !P->w32 || !P->st_in) return SEM_ENOMEM;
-        rc = cuda_check(cudaMallocHost(&P->st_in_host, sizeof(CgState)), "mixed: pinned state");
+        P->st_in_host = static_cast<CgState *>(pinned_slot_alloc());
+        rc = P->st_in_host ? SEM_OK : SEM_ENOMEM;
         if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(P->st_in, 0, sizeof(CgState), stream()), "mixed: state");
         if (rc == SEM_OK) rc = prepare_ax32(P);
     }
@@ -103,7 +104,8 @@ void mixed_release(Problem *P) {
     void *ptrs[] = {P->G32, P->G16, P->d32, P->r32, P->p32, P->w32, P->st_in};
     for (void *q : ptrs)
         if (q) dev_free(q);
-    if (P->st_in_host) cudaFreeHost(P->st_in_host);
+    pinned_slot_free(P->st_in_host);
+    P->st_in_host = nullptr;
 }
 
 static int graph32_iters_for(const Problem *P) { return P->nL < (1 << 20) ? 64 : 32; }

@@ -388,7 +388,10 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         if (!P->x || !P->r || !P->p || !P->w || !P->partials || !P->st) rc = SEM_ENOMEM;
     }
     if (rc == SEM_OK) rc = prepare_ax(P);
-    if (rc == SEM_OK) rc = cuda_check(cudaMallocHost(&P->st_host, sizeof(CgState)), "mesh: pinned state");
+    if (rc == SEM_OK) {
+        P->st_host = static_cast<CgState *>(pinned_slot_alloc());
+        if (!P->st_host) rc = SEM_ENOMEM;
+    }
     if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(P->st, 0, sizeof(CgState), stream()), "mesh: state");
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
     if (rc != SEM_OK) {
@@ -444,7 +447,7 @@ void problem_destroy(Problem *P) {
     for (int32_t *q : iptrs)
         if (q) dev_free(q);
     if (P->st) dev_free(P->st);
-    if (P->st_host) cudaFreeHost(P->st_host);
+    pinned_slot_free(P->st_host);
     delete P;
 }
 

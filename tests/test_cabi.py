@@ -40,6 +40,8 @@ def test_binding_names_match_exports():
 
 def test_calls_before_init_return_einit(lib):
     from paper_2606_12650_gb300 import sem
+    if sem._keep.get("initialised"):
+        pytest.skip("libsem was initialised by an earlier test in this process")
     buf = (ctypes.c_double * 4)()
     assert lib.sem_update(ctypes.cast(buf, ctypes.c_void_p), 0, 4, 8, sem.SEM_TO) == sem.SEM_EINIT
     assert "not initialised" in sem.last_error()
@@ -51,6 +53,8 @@ def test_calls_before_init_return_einit(lib):
 
 def test_allocator_hooks_must_come_in_pairs(lib):
     from paper_2606_12650_gb300 import sem
+    if sem._keep.get("initialised"):
+        pytest.skip("libsem was initialised by an earlier test in this process")
     fn = sem.ALLOC_FN(lambda n, c: 0)
     assert lib.sem_set_allocator(ctypes.cast(fn, ctypes.c_void_p), None, None) == sem.SEM_EARG
     assert lib.sem_set_allocator(None, None, None) == sem.SEM_OK
@@ -83,6 +87,8 @@ def test_autotune_table_is_checked_at_init(lib, tmp_path):
     touched (kind, N in [1, 9], variant available for the kind, elements per
     block fitting one block); a bad file fails sem_init with SEM_EARG."""
     from paper_2606_12650_gb300 import sem
+    if sem._keep.get("initialised"):
+        pytest.skip("libsem was initialised by an earlier test in this process")
 
     def init(*args):
         arr = (ctypes.c_char_p * len(args))(*[a.encode() for a in args])
