@@ -114,7 +114,7 @@ struct Batch {
     BatchCtl *ctl_host = nullptr;
     unsigned seen_finished = 0;
     bool any_init = false;
-    int grid_ax64 = 0, grid_ax32 = 0, grid_vec = 0;
+    int grid_ax64 = 0, grid_ax32 = 0;   // resident CTAs of the operator launches
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
 };
@@ -621,8 +621,6 @@ static int batch_attrs(Batch *B) {
     if (rc == SEM_OK)
         rc = batch_grid(reinterpret_cast<const void *>(batch_ax_kernel<float, __nv_bfloat16, 2>),
                         batch_ax_smem<float>(), &B->grid_ax32);
-    if (rc == SEM_OK)
-        rc = batch_grid(reinterpret_cast<const void *>(batch_vec_kernel<kVecUpdate64>), 0, &B->grid_vec);
     int g = 0;
     if (rc == SEM_OK) rc = vec_grid<kVecUpdate64>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecUpdate32>(&g);
