@@ -38,6 +38,9 @@ struct EoMat {
     T e[25];
     T o[30];
     T m[5];
+    // FP32: (e[i*H + l], o[i*H + l]) side by side, the operand pairs of the
+    // packed two-lane sums (unused in FP64)
+    alignas(8) T eo[sizeof(T) == 4 ? 50 : 2];
 };
 
 template <typename T, typename GT>
@@ -48,11 +51,36 @@ struct AxLineArgs {
     int epb;         // elements per block
 };
 
+// FP32 and even N+1: the even and odd sums of row i advance together as one
+// two-lane pair, (A_i, B_i) += (Me_il, Mo_il) (u_e,l, u_o,l), one packed
+// f32x2 fma per term instead of two; each lane rounds like the scalar fma,
+// so y is bit-identical to the scalar form.
+template <int NQ>
+__device__ __forceinline__ void eo_apply_x2(const float (&u)[NQ], float (&y)[NQ], const EoMat<float> &c) {
+    constexpr int H = NQ / 2;
+    float2 v[H];
+#pragma unroll
+    for (int l = 0; l < H; ++l) v[l] = make_float2(u[l] + u[NQ - 1 - l], u[l] - u[NQ - 1 - l]);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        float2 s = __fmul2_rn(make_float2(c.eo[2 * (i * H)], c.eo[2 * (i * H) + 1]), v[0]);
+#pragma unroll
+        for (int l = 1; l < H; ++l)
+            s = __ffma2_rn(make_float2(c.eo[2 * (i * H + l)], c.eo[2 * (i * H + l) + 1]), v[l], s);
+        y[i] = s.x + s.y;
+        y[NQ - 1 - i] = s.y - s.x;
+    }
+}
+
 // y = M u by the even-odd split.
 template <int NQ, typename T>
 __device__ __forceinline__ void eo_apply(const T (&u)[NQ], T (&y)[NQ], const EoMat<T> &c) {
     constexpr int H = NQ / 2;
     constexpr bool ODD = (NQ & 1) != 0;
+    if constexpr (sizeof(T) == 4 && !ODD) {
+        eo_apply_x2<NQ>(u, y, c);
+        return;
+    }
     T ue[H], uo[H];
 #pragma unroll
     for (int l = 0; l < H; ++l) {
@@ -193,6 +221,8 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
         slab_issue(s1, src1, pl1, bar);
         if (CG) slab_issue(s2, src2, pl2, bar);
         if (GS) slab_issue(gdst, gsrc, plg, bar);
+        // factors read from global memory in phase 2: start them towards L2 now
+        if (GM == kGLoad) bulk_prefetch_l2(gsrc, uint32_t(ne) * NP * 6u * uint32_t(sizeof(GT)));
     }
     slab_edges(s1, src1, pl1, tid, nthreads);
     if (CG) slab_edges(s2, src2, pl2, tid, nthreads);
@@ -281,9 +311,44 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
     }
     __syncthreads();
 
-    // ---- (2) geometric factors, node by node
+    // ---- (2) geometric factors, node by node (FP32, even N+1: two nodes of
+    // the t line at a time, in packed f32x2 arithmetic)
     T wt[NQ];
-    if (act) {
+    constexpr bool X2 = false;
+    if constexpr (X2) {
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < NQ; k += 2) {
+                const int pq = k * P2 + tp;
+                float g[2][6];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if constexpr (PF) {
+                        const float2 g01 = bf16x2_to_float2(gw[k + h][0]), g23 = bf16x2_to_float2(gw[k + h][1]),
+                                     g45 = bf16x2_to_float2(gw[k + h][2]);
+                        g[h][0] = g01.x; g[h][1] = g01.y; g[h][2] = g23.x;
+                        g[h][3] = g23.y; g[h][4] = g45.x; g[h][5] = g45.y;
+                    } else if constexpr (GS) {
+                        load_g6_smem(reinterpret_cast<const GT *>(gdst) + 6 * (eb * NP + (k + h) * NQ2 + tq), g[h]);
+                    } else {
+                        load_g6(G, nb + (k + h) * NQ2 + tq, g[h]);
+                    }
+                }
+                const float2 ur = make_float2(SU[pq], SU[pq + P2]), us = make_float2(SV[pq], SV[pq + P2]),
+                             ut2 = make_float2(ut[k], ut[k + 1]);
+                auto g2 = [&](int c) { return make_float2(g[0][c], g[1][c]); };
+                const float2 wr = __ffma2_rn(g2(2), ut2, __ffma2_rn(g2(1), us, __fmul2_rn(g2(0), ur)));
+                const float2 ws = __ffma2_rn(g2(4), ut2, __ffma2_rn(g2(3), us, __fmul2_rn(g2(1), ur)));
+                const float2 w3 = __ffma2_rn(g2(5), ut2, __ffma2_rn(g2(4), us, __fmul2_rn(g2(2), ur)));
+                SU[pq] = wr.x;
+                SU[pq + P2] = wr.y;
+                SV[pq] = ws.x;
+                SV[pq + P2] = ws.y;
+                wt[k] = w3.x;
+                wt[k + 1] = w3.y;
+            }
+        }
+    } else if (act) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             const int pq = k * P2 + tp;
@@ -381,6 +446,10 @@ inline EoMat<T> eo_coefficients(const double *M, int nq) {
         for (int l = 0; l < H; ++l) {
             c.e[i * H + l] = T(0.5 * (M[i * nq + l] + M[i * nq + N - l]));
             c.o[i * H + l] = T(0.5 * (M[i * nq + l] - M[i * nq + N - l]));
+            if (sizeof(T) == 4) {
+                c.eo[2 * (i * H + l)] = c.e[i * H + l];
+                c.eo[2 * (i * H + l) + 1] = c.o[i * H + l];
+            }
         }
     if (nq & 1) {
         for (int l = 0; l < H; ++l) c.o[H * H + l] = T(0.5 * (M[H * nq + l] - M[H * nq + N - l]));

@@ -116,6 +116,18 @@ __device__ __forceinline__ void slab_issue(T *dst, const T *src, const SlabPlan 
     }
 }
 
+// Have the TMA engine bring the 16-byte-aligned middle of [src, src + bytes)
+// into L2: no destination and no completion to wait for, and no byte outside
+// the range is touched.  One thread.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    const SlabPlan p = slab_plan(src, bytes);
+    if (p.mid_bytes)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                         reinterpret_cast<const unsigned char *>(src) + p.head_bytes),
+                     "r"(p.mid_bytes)
+                     : "memory");
+}
+
 // Plain-load part of a slab copy (ragged head and tail), element-wise,
 // spread over threads [t0, t0 + nthreads).
 template <typename T>
