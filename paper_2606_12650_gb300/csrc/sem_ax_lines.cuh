@@ -311,44 +311,9 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
     }
     __syncthreads();
 
-    // ---- (2) geometric factors, node by node (FP32, even N+1: two nodes of
-    // the t line at a time, in packed f32x2 arithmetic)
+    // ---- (2) geometric factors, node by node
     T wt[NQ];
-    constexpr bool X2 = false;
-    if constexpr (X2) {
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < NQ; k += 2) {
-                const int pq = k * P2 + tp;
-                float g[2][6];
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if constexpr (PF) {
-                        const float2 g01 = bf16x2_to_float2(gw[k + h][0]), g23 = bf16x2_to_float2(gw[k + h][1]),
-                                     g45 = bf16x2_to_float2(gw[k + h][2]);
-                        g[h][0] = g01.x; g[h][1] = g01.y; g[h][2] = g23.x;
-                        g[h][3] = g23.y; g[h][4] = g45.x; g[h][5] = g45.y;
-                    } else if constexpr (GS) {
-                        load_g6_smem(reinterpret_cast<const GT *>(gdst) + 6 * (eb * NP + (k + h) * NQ2 + tq), g[h]);
-                    } else {
-                        load_g6(G, nb + (k + h) * NQ2 + tq, g[h]);
-                    }
-                }
-                const float2 ur = make_float2(SU[pq], SU[pq + P2]), us = make_float2(SV[pq], SV[pq + P2]),
-                             ut2 = make_float2(ut[k], ut[k + 1]);
-                auto g2 = [&](int c) { return make_float2(g[0][c], g[1][c]); };
-                const float2 wr = __ffma2_rn(g2(2), ut2, __ffma2_rn(g2(1), us, __fmul2_rn(g2(0), ur)));
-                const float2 ws = __ffma2_rn(g2(4), ut2, __ffma2_rn(g2(3), us, __fmul2_rn(g2(1), ur)));
-                const float2 w3 = __ffma2_rn(g2(5), ut2, __ffma2_rn(g2(4), us, __fmul2_rn(g2(2), ur)));
-                SU[pq] = wr.x;
-                SU[pq + P2] = wr.y;
-                SV[pq] = ws.x;
-                SV[pq + P2] = ws.y;
-                wt[k] = w3.x;
-                wt[k + 1] = w3.y;
-            }
-        }
-    } else if (act) {
+    if (act) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) {
             const int pq = k * P2 + tp;
