@@ -96,3 +96,7 @@ def test_reference_arm_line_on_rank_zero(oracle_mod):
               "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in line, k
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    cb = line["cpu_baseline"]
+    # one oracle process per host core that fits in memory, or the single-threaded oracle
+    assert cb["cores"] >= 1 and cb["value"] == line["value"]
+    assert ("independent processes" in cb["sample"]) == (cb["cores"] > 1)
