@@ -27,19 +27,20 @@ bool g_init = false;
 uint64_t g_epoch = 1;
 
 // Built-in table: the winners of tuning runs on GB300 with ~17 M local
-// nodes per problem (E = 64^3 at N = 3 down to 26^3 at N = 9; CG operator,
-// 10 launches per candidate), as {variant, elements per block} for
-// N = 1..9; the run-time tuner replaces entries for the problems at hand.
+// nodes per problem (E = 128^3 at N = 1 down to 26^3 at N = 9; CG operator,
+// 10 launches per candidate), as {variant, elements per block} indexed by
+// N + 1 (entries 0 and 1 unused); the run-time tuner replaces entries for
+// the problems at hand.
 struct DefaultEntry {
     int variant, epb;
 };
 constexpr DefaultEntry kDefault[kTuneKinds][kMaxQ + 1] = {
     // FP64
-    {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 15}, {1, 7}, {1, 7}, {1, 4}, {1, 6}, {1, 5}},
+    {{0, 0}, {0, 0}, {1, 96}, {1, 56}, {1, 32}, {1, 10}, {1, 7}, {1, 7}, {1, 8}, {1, 3}, {1, 2}},
     // FP32, FP32 factors
-    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 8}, {1, 4}, {1, 5}},
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 6}, {1, 4}, {1, 3}},
     // FP32, BF16 factors
-    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {3, 20}, {3, 7}, {1, 10}, {3, 4}, {1, 6}, {3, 3}},
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 8}, {1, 6}, {1, 3}},
 };
 
 TuneChoice default_choice(int kind, int nq) {
