@@ -252,9 +252,10 @@ ax_kernel(const AxArgs<T, GT> P) {
         return;
     if (CG) {
         // the column's partial is formed in T; the block and grid sums are FP64
+        // (the grid sum over groups of blocks)
         const double bs = block_sum(double(part), red);
-        if (publish_partial(bs, P.partials, &P.st->ticket_ax)) {
-            const double pap = finish_partials(P.partials, int(gridDim.x), &P.st->ticket_ax, red);
+        if (publish_grouped(bs, P.partials, &P.st->ticket_ax)) {
+            const double pap = finish_grouped(P.partials, &P.st->ticket_ax);
             if (threadIdx.x == 0) {
                 P.st->pap = pap;
                 P.st->alpha = P.st->rho / pap;

@@ -371,7 +371,6 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
 template <int NQ, typename T, typename GT, bool CG, bool PRE, int GM = kGLoad>
 __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red[32];
     const AxArgs<T, GT> &A = P.a;
     if (CG && A.st->done) return;  // solve finished: the rest of the graph is a no-op
 
@@ -389,11 +388,16 @@ __global__ void __launch_bounds__(512) ax_lines_kernel(const AxLineArgs<T, GT> P
                                              A.dinv, e0, ne, P.epb, regA, bar, 0u, A.status, &part))
         return;
     if (CG) {
-        // the thread's partial is formed in T; the block and grid sums are FP64
-        // (the slab regions are free now and hold the block's partials)
-        const double bs = block_sum_wide(double(part), reinterpret_cast<double *>(regA));
-        if (publish_partial(bs, A.partials, &A.st->ticket_ax)) {
-            const double pap = finish_partials(A.partials, int(gridDim.x), &A.st->ticket_ax, red);
+        // the thread's partial is formed in T; the block sum in T for FP32
+        // (FP64 for FP64), the grid sum in FP64 over groups of blocks (the
+        // slab regions are free now and hold the block's partials)
+        double bs;
+        if constexpr (sizeof(T) == 4)
+            bs = double(block_sum_f32(part, reinterpret_cast<float *>(regA)));
+        else
+            bs = block_sum_wide(double(part), reinterpret_cast<double *>(regA));
+        if (publish_grouped(bs, A.partials, &A.st->ticket_ax)) {
+            const double pap = finish_grouped(A.partials, &A.st->ticket_ax);
             if (threadIdx.x == 0) {
                 A.st->pap = pap;
                 A.st->alpha = A.st->rho / pap;

@@ -304,9 +304,11 @@ __global__ void assemble_box_kernel(const double *__restrict__ f, double *__rest
 
 // One CG update step over all local nodes (grid-stride), with the <r, r>
 // reduction: per-thread partials in Acc, block and grid sums in FP64, and the
-// last block closes the iteration (beta, counter, stop flag).
+// last block closes the iteration (beta, counter, stop flag).  Bounded to 48
+// registers so that 5 blocks of 256 threads stay resident per SM: the FP32
+// step is latency-bound (E = 32^3, N = 7: inner iteration -3 %).
 template <int NQ, typename T, typename Acc>
-__global__ void __launch_bounds__(256) cg_update_nodes_kernel(T *__restrict__ x, T *__restrict__ r,
+__global__ void __launch_bounds__(256, 5) cg_update_nodes_kernel(T *__restrict__ x, T *__restrict__ r,
                                                               const T *__restrict__ p, const T *__restrict__ w,
                                                               int nL, BoxDims bd, double *partials, CgState *st) {
     __shared__ double red[32];

@@ -204,6 +204,87 @@ __device__ __forceinline__ double finish_partials(const double *partials, int n,
     return acc;
 }
 
+// Two-level grid sum for launches of many blocks.  Each block publishes into
+// its group of kSumGroup consecutive blocks; the group's last block to arrive
+// sums the group's partials in order (one warp, fixed shuffle tree), stores
+// the group sum, resets the group ticket and takes a ticket of the grid; the
+// last group returns true in all threads of its block, and finish_grouped
+// then sums the group sums in order.  The FP64 additions of the grid sum are
+// spread over the groups' last blocks instead of all falling on one block at
+// the end of the launch (on GB300 FP64 runs at 1/64 of the FP32 rate).
+__device__ __forceinline__ bool publish_grouped(double v0, double *partials, uint32_t *ticket) {
+    __shared__ int s_last;
+    uint32_t *gt = group_tickets(partials);
+    const int b = int(blockIdx.x), g = b / kSumGroup, g0 = g * kSumGroup;
+    const int gn = min(kSumGroup, int(gridDim.x) - g0);
+    if (threadIdx.x == 0) {
+        partials[b] = v0;
+        __threadfence();
+        s_last = atomicAdd(gt + g, 1u) == uint32_t(gn - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __syncthreads();  // every thread has read s_last before thread 0 rewrites it
+    if (threadIdx.x < 32) {
+        __threadfence();
+        double s = int(threadIdx.x) < gn ? __ldcg(partials + g0 + threadIdx.x) : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) {
+            partials[kMaxPartials + g] = s;
+            gt[g] = 0u;
+            __threadfence();
+            const uint32_t ng = (gridDim.x + kSumGroup - 1) / kSumGroup;
+            s_last = atomicAdd(ticket, 1u) == ng - 1;
+        }
+    }
+    __syncthreads();
+    return s_last != 0;
+}
+
+// Zero the group tickets (grid-stride): at the start of every solve, so that
+// a launch that gave up half-way (a timed-out copy) leaves no stale count.
+__device__ __forceinline__ void reset_group_tickets(double *partials) {
+    uint32_t *gt = group_tickets(partials);
+    for (int i = int(blockIdx.x * blockDim.x + threadIdx.x); i < kMaxSumGroups; i += int(gridDim.x * blockDim.x))
+        gt[i] = 0u;
+}
+
+// In the block for which publish_grouped returned true: the sum of the group
+// sums in a fixed order (one warp), the grid ticket reset.  Result in thread 0.
+__device__ __forceinline__ double finish_grouped(const double *partials, uint32_t *ticket) {
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        __threadfence();
+        const int ng = int((gridDim.x + kSumGroup - 1) / kSumGroup);
+        for (int q = threadIdx.x; q < ng; q += 32) s += __ldcg(partials + kMaxPartials + q);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) *ticket = 0u;
+    }
+    return s;
+}
+
+// Block sum of FP32 values in FP32: fixed shuffle tree per warp, then the
+// warp sums in order by warp 0.  scratch: >= 32 floats of shared memory that
+// the block may still be reading (the first barrier protects it).  Result in
+// thread 0.
+__device__ __forceinline__ float block_sum_f32(float v, float *scratch) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    float s = 0.f;
+    if (wid == 0) {
+        s = lane < nw ? scratch[lane] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;
+}
+
 // Two-value variants (PCG: <r, z> and <r, r>): slots partials[2b], [2b+1].
 __device__ __forceinline__ bool publish_partial2(double v0, double v1, double *partials, uint32_t *ticket) {
     __shared__ int s_last2;

@@ -16,6 +16,17 @@ namespace sem {
 
 constexpr int kMaxQ = 10;          // N <= 9  ->  N+1 <= 10 points per direction
 constexpr int kMaxPartials = 1 << 17;
+// Grid sums of many blocks in two levels (publish_grouped): groups of
+// kSumGroup consecutive blocks.  A problem's partials buffer holds
+// kMaxPartials block partials, then kMaxSumGroups group sums (doubles), then
+// kMaxSumGroups group tickets (uint32, zero between launches).
+constexpr int kSumGroup = 32;
+constexpr int kMaxSumGroups = kMaxPartials / kSumGroup;
+constexpr size_t kPartialsBytes =
+    sizeof(double) * (kMaxPartials + kMaxSumGroups) + sizeof(uint32_t) * kMaxSumGroups;
+__host__ __device__ inline uint32_t *group_tickets(double *partials) {
+    return reinterpret_cast<uint32_t *>(partials + kMaxPartials + kMaxSumGroups);
+}
 
 // Small per-problem constants passed to kernels by value (constant bank).
 struct OpConsts {

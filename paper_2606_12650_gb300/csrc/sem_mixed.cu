@@ -31,6 +31,7 @@ __global__ void mixed_inner_init_kernel(const double *__restrict__ r64, const do
                                         int maxit, double tol) {
     __shared__ double red[32];
     double acc = 0.0;
+    reset_group_tickets(partials);
     for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < n;
          l += int64_t(gridDim.x) * blockDim.x) {
         const float v = __double2float_rn(r64[l]);

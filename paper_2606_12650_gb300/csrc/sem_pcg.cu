@@ -86,6 +86,7 @@ __global__ void pcg_init_kernel(const double *__restrict__ b, const double *__re
                                 double tol, double *hist) {
     __shared__ double red[32];
     double a0 = 0.0, a1 = 0.0;
+    reset_group_tickets(partials);
     for (int64_t l = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; l < n; l += int64_t(gridDim.x) * blockDim.x) {
         const double bl = b[l];
         x[l] = 0.0;

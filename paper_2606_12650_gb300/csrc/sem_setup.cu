@@ -383,7 +383,7 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         P->r = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->p = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->w = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
-        P->partials = static_cast<double *>(dev_alloc(sizeof(double) * kMaxPartials));
+        P->partials = static_cast<double *>(dev_alloc(kPartialsBytes));
         P->st = static_cast<CgState *>(dev_alloc(sizeof(CgState)));
         if (!P->x || !P->r || !P->p || !P->w || !P->partials || !P->st) rc = SEM_ENOMEM;
     }
@@ -393,6 +393,9 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         if (!P->st_host) rc = SEM_ENOMEM;
     }
     if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(P->st, 0, sizeof(CgState), stream()), "mesh: state");
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemsetAsync(group_tickets(P->partials), 0, sizeof(uint32_t) * kMaxSumGroups, stream()),
+                        "mesh: group tickets");
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
     if (rc != SEM_OK) {
         problem_destroy(P);

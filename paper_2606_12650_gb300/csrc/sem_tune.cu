@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 
+#include "sem_device.cuh"
 #include "sem_internal.h"
 
 namespace sem {
@@ -100,7 +101,9 @@ __global__ void tune_fill_kernel(T *r, T *p, int64_t n) {
     }
 }
 
-__global__ void tune_state_kernel(CgState *st) {
+__global__ void tune_state_kernel(CgState *st, double *partials) {
+    reset_group_tickets(partials);
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     st->alpha = 0.0;
     st->beta = 0.0;
     st->rho = 1.0;
@@ -154,7 +157,7 @@ int tune_problem(Problem *P, int kind, int reps, double *cand, int cap, int *n_c
         tune_fill_kernel<double><<<blocks, 256, 0, stream()>>>(P->r, P->p, P->nL);
     else
         tune_fill_kernel<float><<<blocks, 256, 0, stream()>>>(P->r32, P->p32, P->nL);
-    tune_state_kernel<<<1, 1, 0, stream()>>>(st);
+    tune_state_kernel<<<1, 256, 0, stream()>>>(st, P->partials);
     count_launches(2);
     rc = cuda_check(cudaGetLastError(), "autotune: set-up");
     if (rc != SEM_OK) return rc;
