@@ -311,7 +311,7 @@ template <int NQ, typename T, typename Acc>
 __global__ void __launch_bounds__(256, 5) cg_update_nodes_kernel(T *__restrict__ x, T *__restrict__ r,
                                                               const T *__restrict__ p, const T *__restrict__ w,
                                                               int nL, BoxDims bd, double *partials, CgState *st) {
-    __shared__ double red[32];
+    __shared__ double scratch[256];
     if (st->done) return;
     const T alpha = T(st->alpha);
     Acc acc = Acc(0);
@@ -319,9 +319,15 @@ __global__ void __launch_bounds__(256, 5) cg_update_nodes_kernel(T *__restrict__
     const int nv = nL / V;   // nL is a multiple of (N+1), hence of V
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nv; u += gridDim.x * blockDim.x)
         update_vec<NQ, V, T, Acc>(x, r, p, w, u * V, bd, alpha, acc);
-    const double bs = block_sum(double(acc), red);
-    if (publish_partial(bs, partials, &st->ticket_up)) {
-        const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
+    // all blocks of the resident wave reach this point together: block sums
+    // in Acc when it is FP32, one warp's FP64 sum otherwise, grid sum in groups
+    double bs;
+    if constexpr (sizeof(Acc) == 4)
+        bs = double(block_sum_f32(acc, reinterpret_cast<float *>(scratch)));
+    else
+        bs = block_sum_wide(double(acc), scratch);
+    if (publish_grouped(bs, partials, &st->ticket_up)) {
+        const double rho_new = finish_grouped(partials, &st->ticket_up);
         if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
     }
 }
@@ -332,7 +338,7 @@ template <int NQ, typename T, typename Acc>
 __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x, T *__restrict__ r,
                                                               const T *__restrict__ p, const T *__restrict__ w,
                                                               int nL, BoxDims bd, double *partials, CgState *st) {
-    __shared__ double red[32];
+    __shared__ double scratch[256];
     if (st->done) return;
     constexpr int V = UpdVec<NQ, T>::value;
     using RM = RowMap<NQ, V>;
@@ -346,9 +352,11 @@ __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x,
         const int l0 = RM::l0(task, lane, E);
         if (l0 >= 0) update_vec<NQ, V, T, Acc, false, true>(x, r, p, w, l0, bd, alpha, acc);
     }
-    const double bs = block_sum(double(acc), red);
-    if (publish_partial(bs, partials, &st->ticket_up)) {
-        const double rho_new = finish_partials(partials, int(gridDim.x), &st->ticket_up, red);
+    // one warp's FP64 sum per block (13 instead of 40 warp-wide FP64 adds),
+    // grid sum in groups
+    const double bs = block_sum_wide(double(acc), scratch);
+    if (publish_grouped(bs, partials, &st->ticket_up)) {
+        const double rho_new = finish_grouped(partials, &st->ticket_up);
         if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
     }
 }
