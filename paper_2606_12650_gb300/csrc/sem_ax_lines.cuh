@@ -221,8 +221,10 @@ __device__ __forceinline__ bool lines_group(const T *x, T *y, T *p, const GT *G,
         slab_issue(s1, src1, pl1, bar);
         if (CG) slab_issue(s2, src2, pl2, bar);
         if (GS) slab_issue(gdst, gsrc, plg, bar);
-        // factors read from global memory in phase 2: start them towards L2 now
-        if (GM == kGLoad) bulk_prefetch_l2(gsrc, uint32_t(ne) * NP * 6u * uint32_t(sizeof(GT)));
+        // FP32: the factors read from global memory in phase 2 start towards L2
+        // now (in FP64 a block computes so long that prefetched lines would be
+        // evicted before phase 2 reads them)
+        if (GM == kGLoad && sizeof(T) == 4) bulk_prefetch_l2(gsrc, uint32_t(ne) * NP * 6u * uint32_t(sizeof(GT)));
     }
     slab_edges(s1, src1, pl1, tid, nthreads);
     if (CG) slab_edges(s2, src2, pl2, tid, nthreads);

@@ -37,11 +37,11 @@ struct DefaultEntry {
 };
 constexpr DefaultEntry kDefault[kTuneKinds][kMaxQ + 1] = {
     // FP64
-    {{0, 0}, {0, 0}, {1, 96}, {1, 56}, {1, 32}, {1, 10}, {1, 7}, {1, 7}, {1, 8}, {1, 3}, {1, 2}},
+    {{0, 0}, {0, 0}, {0, 0}, {1, 28}, {0, 0}, {1, 10}, {1, 7}, {1, 7}, {1, 3}, {1, 3}, {1, 2}},
     // FP32, FP32 factors
-    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 6}, {1, 4}, {1, 3}},
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 10}, {1, 10}, {1, 5}, {1, 3}, {1, 3}, {1, 2}},
     // FP32, BF16 factors
-    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 20}, {1, 14}, {1, 10}, {1, 8}, {1, 6}, {1, 3}},
+    {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 10}, {4, 7}, {1, 5}, {1, 2}, {1, 1}, {1, 2}},
 };
 
 TuneChoice default_choice(int kind, int nq) {
