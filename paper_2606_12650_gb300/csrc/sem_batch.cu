@@ -774,12 +774,14 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
             q.outer_done = 0;
             any_init = true;
         }
-        // operator body and elements per pass from the tuner's table; an item
-        // holds several passes (~kAxItemNodes local nodes)
+        // operator body from the tuner's table; a pass of the line body fills
+        // the engine's fixed 256-thread CTA (the table's elements per block
+        // size stand-alone blocks, whose count per SM varies with it); an
+        // item holds several passes (~kAxItemNodes local nodes)
         const int full = kBatchThreads / (P->nq * P->nq);
         const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
         const bool lines = c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged;
-        const int group = lines ? std::max(1, std::min(c.epb, full)) : full;
+        const int group = full;
         const int np = P->nq * P->nq * P->nq;
         const int per_item = group * std::max(1, kAxItemNodes / (np * group));
         q.ax_first = int(ax.size());
