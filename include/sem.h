@@ -161,7 +161,8 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               Mixed-precision iterative refinement: from x = 0 the FP64
  *               residual r = b - A x is recomputed after each inner CG solve
  *               of A d = r run in FP32 (FP32 vectors and arithmetic, G in FP32
- *               or BF16, dot sums, alpha and beta in FP64) until its residual
+ *               or BF16; dot products summed per thread and per block in FP32
+ *               and across blocks in FP64; alpha and beta in FP64) until its residual
  *               fell by max(inner_tol, 0.5 tol/||r||) (relative), and x += d
  *               in FP64; stops when ||b - A x||_c/||b||_c <= tol or after
  *               max_outer corrections.  rel_res is that true residual;
@@ -191,7 +192,7 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               operator (reps timed launches after 2 warm-ups, on the
  *               problem's own CG vectors, which it overwrites) and keeps the
  *               fastest.  cand receives (variant, epb, microseconds per
- *               launch) per candidate, n_cand their number (<= 16).
+ *               launch) per candidate, n_cand their number (<= 24).
  *   "autotune_get" kind, N, OUT variant, OUT epb, OUT us
  *   "autotune_set" kind, N, variant, epb      SEM_EARG if the variant does
  *               not exist for the kind or epb does not fit a block
