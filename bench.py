@@ -577,7 +577,7 @@ def run_mixed(a, M, b, x64, t64_ms, job, stream, sem, torch):
     err10 = float((xm10 - x10).abs().max().item() / x10.abs().max().item())
     return {"metric": METRIC, "value": dofs / (t_ms * 1e-3) / 1e9, "unit": "GDOF/s",
             "gdofs_counts": "inner FP32 CG iterations (E N^3 per iteration)",
-            "dtype": "f32 inner CG, bf16 geometric factors, f64 refinement/dots/alpha/beta",
+            "dtype": "f32 inner CG (dots: f32 per block, f64 across blocks), bf16 geometric factors, f64 refinement/alpha/beta",
             "workload": f"same problem, mixed-precision refinement to {a.tol:g} (inner tolerance {a.inner_tol:g})",
             "ms_per_solve": t_ms / a.steps, "solves_per_s": 1e3 * a.steps / t_ms * world,
             "fp64_solves_per_s": 1e3 * a.steps / t64_ms * world,
