@@ -247,6 +247,9 @@ def time_oracle_replicas(a, iters, steps):
     most half of the free host memory.  Returns (processes, per-step times of
     the slowest process, host cores) or None if fewer than two fit."""
     import multiprocessing as mp
+
+    import oracle
+    oracle.build()   # once here, not in every spawned process
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
