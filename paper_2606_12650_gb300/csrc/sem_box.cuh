@@ -303,8 +303,9 @@ __global__ void assemble_box_kernel(const double *__restrict__ f, double *__rest
 }
 
 // One CG update step over all local nodes (grid-stride), with the <r, r>
-// reduction: per-thread partials in Acc, block and grid sums in FP64, and the
-// last block closes the iteration (beta, counter, stop flag).  Bounded to 48
+// reduction: per-thread partials and block sums in Acc, the grid sum in FP64
+// over groups of blocks, and the block that completes it closes the
+// iteration (beta, counter, stop flag).  Bounded to 48
 // registers so that 5 blocks of 256 threads stay resident per SM: the FP32
 // step is latency-bound (E = 32^3, N = 7: inner iteration -3 %).
 template <int NQ, typename T, typename Acc>

@@ -16,15 +16,16 @@
 //   2. cg_update_class_kernel (sem_box.cuh): every local node sums the copies
 //      of w of its global node in ascending local index (the direct-stiffness
 //      sum), then applies r -= alpha (QQ^T w) to itself; <r, r> is
-//      accumulated once per global node; the last block forms rho, beta, the
-//      iteration count and the stop flag.
+//      accumulated once per global node; the block that completes the grid
+//      sum forms rho, beta, the iteration count and the stop flag.
 // Moving x += alpha p into the next operator kernel (which has p in shared
 // memory anyway) takes 24 of the update's 48 bytes per node off HBM and one
 // FP64 operation off the update; x_finish_kernel applies the last one.
 // The dot products of the paper are tree reductions (Section VIII-B, the
 // unrolled reduction of Table "HIP-variable vs HIP-fixed"); here each block
-// reduces in a fixed order and the last block to finish sums the per-block
-// partials in index order, so results are reproducible run to run.  Scalars
+// reduces in a fixed order, the last block of each group of 32 blocks sums
+// the group's partials in index order and the last group sums the group sums
+// (publish_grouped), so results are reproducible run to run.  Scalars
 // never leave the device inside the loop: the host replays a CUDA graph of K
 // iterations and polls the stop flag once per replay.
 #include <cuda_runtime.h>
