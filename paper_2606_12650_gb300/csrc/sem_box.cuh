@@ -212,22 +212,62 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
                 lo[c] = hi[c] = T(0);
             }
         }
+        if constexpr (V == NQ) {
+            // one piece is the whole row: node 0 and node N may both have an
+            // r-face neighbour
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const bool first_lo = (v == 0) && has_lo;
-            const bool last_hi = (v == V - 1) && has_hi;
-            T s = first_lo ? lo[0] + wv[0][v] : wv[0][v];
-            if (last_hi) s = s + hi[0];
+            for (int v = 0; v < V; ++v) {
+                const bool first_lo = (v == 0) && has_lo;
+                const bool last_hi = (v == V - 1) && has_hi;
+                T s = first_lo ? lo[0] + wv[0][v] : wv[0][v];
+                if (last_hi) s = s + hi[0];
 #pragma unroll
-            for (int c = 1; c < 4; ++c) {
-                const int cz = c >> 1, cy = c & 1;
-                const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
-                if (!valid) continue;
-                if (first_lo) s = s + lo[c];
-                s = s + wv[c][v];
-                if (last_hi) s = s + hi[c];
+                for (int c = 1; c < 4; ++c) {
+                    const int cz = c >> 1, cy = c & 1;
+                    const bool valid = (cz == 0 || sz) && (cy == 0 || sy);
+                    if (!valid) continue;
+                    if (first_lo) s = s + lo[c];
+                    s = s + wv[c][v];
+                    if (last_hi) s = s + hi[c];
+                }
+                sv[v] = s;
             }
-            sv[v] = s;
+        } else {
+            // The same chain of additions in every lane of a warp (no additions
+            // predicated off): a piece shorter than the row holds at most one
+            // node with an r-face neighbour (node 0 with one below, or node N
+            // with one above).  That node sums, per copy class c in order, the
+            // pair (lower element's copy, upper element's copy) -- (lo, own) or
+            // (own, hi); a piece without such a node runs the chain on its last
+            // node with zeros for the neighbour (x + 0 == x).  The other nodes
+            // sum their own copies.  The operands and their order are those of
+            // the ascending local index, so every copy of a node still gets the
+            // same bits.
+            T spec = T(0), oe = T(0), mid[V];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int cz = c >> 1, cy = c & 1;
+                const bool valid = (cz == 0 || sz) && (cy == 0 || sy);   // c = 0 always
+                if (!valid) continue;
+                const T x = has_lo ? lo[c] : hi[c];              // 0 without a neighbour
+                const T ws = has_lo ? wv[c][0] : wv[c][V - 1];
+                const T a = has_lo ? x : ws, b = has_lo ? ws : x;
+                spec = c == 0 ? a + b : (spec + a) + b;
+                if (V >= 2) {
+                    const T we = has_lo ? wv[c][V - 1] : wv[c][0];
+                    oe = c == 0 ? we : oe + we;
+                }
+#pragma unroll
+                for (int v = 1; v < V - 1; ++v) mid[v] = c == 0 ? wv[c][v] : mid[v] + wv[c][v];
+            }
+            if (V == 1) {
+                sv[0] = spec;
+            } else {
+                sv[0] = has_lo ? spec : oe;
+                sv[V - 1] = has_lo ? oe : spec;
+#pragma unroll
+                for (int v = 1; v < V - 1; ++v) sv[v] = mid[v];
+            }
         }
     }
     const bool owner_row = sy >= 0 && sz >= 0;
