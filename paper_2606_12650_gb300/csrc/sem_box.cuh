@@ -212,9 +212,11 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
                 lo[c] = hi[c] = T(0);
             }
         }
-        if constexpr (V == NQ) {
-            // one piece is the whole row: node 0 and node N may both have an
-            // r-face neighbour
+        if constexpr (V == NQ || sizeof(T) == 4) {
+            // one piece is the whole row (node 0 and node N may both have an
+            // r-face neighbour), or FP32, where additions are cheap and the
+            // step is bound by memory: each node's additions, the neighbour
+            // ones predicated on the lane
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const bool first_lo = (v == 0) && has_lo;
@@ -233,8 +235,9 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
                 sv[v] = s;
             }
         } else {
-            // The same chain of additions in every lane of a warp (no additions
-            // predicated off): a piece shorter than the row holds at most one
+            // FP64: the same chain of additions in every lane of a warp (no
+            // additions predicated off, which would still take FP64 issue
+            // slots at 1/64 rate): a piece shorter than the row holds at most one
             // node with an r-face neighbour (node 0 with one below, or node N
             // with one above).  That node sums, per copy class c in order, the
             // pair (lower element's copy, upper element's copy) -- (lo, own) or
