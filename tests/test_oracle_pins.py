@@ -138,6 +138,32 @@ def test_geometry_matches_analytic_jacobian(oracle_mod):
                             l += 1
 
 
+def test_relative_nodes_are_nodes_minus_element_origin(oracle_mod):
+    """The relative nodal coordinates (the geometry's input) are the nodal
+    coordinates minus each element's first vertex, and the element corners
+    sit on its vertices (the trilinear map interpolates them)."""
+    N, nx, ny, nz = 4, 3, 2, 2
+    verts = box_vertices(nx, ny, nz, 0.05, seed=12)
+    X = oracle_mod.nodes(nx, ny, nz, N, verts)
+    Xr = oracle_mod.nodes_rel(nx, ny, nz, N, verts)
+    n = N + 1
+    npe = n ** 3
+    e = 0
+    for ez in range(nz):
+        for ey in range(ny):
+            for ex in range(nx):
+                V = element_vertices(verts, nx, ny, ex, ey, ez)
+                blk = slice(e * npe, (e + 1) * npe)
+                np.testing.assert_allclose(Xr[blk] + V[0, 0, 0], X[blk], rtol=0, atol=1e-15)
+                Xe = X[blk].reshape(n, n, n, 3)   # [k][j][i]
+                for k in (0, 1):
+                    for j in (0, 1):
+                        for i in (0, 1):
+                            # the node at the element corner is that vertex
+                            np.testing.assert_allclose(Xe[k * N, j * N, i * N], V[k, j, i], rtol=0, atol=1e-15)
+                e += 1
+
+
 # --------------------------------------------------------------------------- Ax
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 7])
 def test_ax_kills_constants_before_mask(oracle_mod, N):
