@@ -2,7 +2,8 @@
 
 Each case plants one mistake in a copy of ``oracle/sem_oracle.c`` (on the CPU,
 in a temporary directory), builds it, and runs the pin suite against it with
-``SEM_ORACLE_LIB`` pointing at the broken library.  The suite must fail.
+``SEM_ORACLE_LIB`` pointing at the broken library.  The suite must fail.  A
+case may name the pins (a ``-k`` expression) that must catch it on their own.
 """
 import os
 import subprocess
@@ -34,12 +35,19 @@ MUTATIONS = {
     "diag_wrong_entry": ("d[(long)np * e + q] = y[q];", "d[(long)np * e + q] = y[0];"),
     "ut_wrong_stride": ("ut += D[k * n + m] * ue[i + n * (j + n * m)];",
                         "ut += D[k * n + m] * ue[i + n * (m + n * j)];"),
+    # the geometry differentiated from absolute coordinates: only ~1e-13 off,
+    # caught by the extended-precision pin at h = 1/32 alone
+    "geometry_from_absolute_coordinates": (
+        "acc += (verts[3 * v + d] - verts[3 * v0 + d]) * hr[a] * hs[b] * ht[c];",
+        "acc += verts[3 * v + d] * hr[a] * hs[b] * ht[c];",
+        "extended_precision"),
 }
 
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(name, tmp_path):
-    before, after = MUTATIONS[name]
+    before, after = MUTATIONS[name][:2]
+    select = ["-k", MUTATIONS[name][2]] if len(MUTATIONS[name]) > 2 else []
     src = open(SRC).read()
     assert src.count(before) == 1, f"mutation anchor for {name} not found exactly once"
     mutated = tmp_path / "sem_oracle_mut.c"
@@ -49,6 +57,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                     str(mutated), "-o", str(lib), "-lm"], check=True)
     env = dict(os.environ, SEM_ORACLE_LIB=str(lib))
     proc = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                           os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                           os.path.join(ROOT, "tests", "test_oracle_pins.py")] + select,
                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
-    assert proc.returncode != 0, f"pins did not catch mutation {name}:\n{proc.stdout[-2000:]}"
+    # a pin must fail (not merely no test run: pytest exits non-zero then too)
+    assert proc.returncode == 1 and " failed" in proc.stdout, \
+        f"pins did not catch mutation {name}:\n{proc.stdout[-2000:]}"

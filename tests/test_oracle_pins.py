@@ -17,7 +17,8 @@ import pytest
 from numpy.polynomial import legendre as L
 
 from paper_2606_12650_gb300.inputs import box_vertices, normal_field
-from weakform import dense_stiffness, element_stiffness, element_vertices, lagrange_derivs
+from weakform import (dense_stiffness, element_stiffness, element_vertices, geometry_extended,
+                      lagrange_derivs)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "gll_closed_forms.json")
 
@@ -136,6 +137,24 @@ def test_geometry_matches_analytic_jacobian(oracle_mod):
                             np.testing.assert_allclose(P.G[l], ref, rtol=1e-12, atol=1e-15)
                             assert abs(P.B[l] - s) < 1e-14
                             l += 1
+
+
+@pytest.mark.parametrize("N", [7, 9])
+def test_geometry_extended_precision_at_benchmark_element_size(oracle_mod, N):
+    """At the benchmark's element size h = 1/32 (32 x 32 x 2 jittered box),
+    the FP64 geometry is within 1e-14 of max|G| of an extended-precision
+    evaluation of the analytic trilinear Jacobian, and B within 1e-14 of
+    max|B|.  The oracle reaches this by differentiating coordinates relative
+    to each element's first vertex: from absolute O(1) coordinates the
+    rounding of the position, amplified by sum_m |D_im| / h, costs ~1.5e-13."""
+    nx, ny, nz = 32, 32, 2
+    verts = box_vertices(nx, ny, nz, 0.05, seed=2)
+    P = oracle_mod.Problem(nx, ny, nz, N, verts)
+    G_ext, B_ext = geometry_extended(verts, nx, ny, nz, P.xi, P.w)
+    g_err = float(np.max(np.abs(P.G - G_ext)) / np.max(np.abs(G_ext)))
+    b_err = float(np.max(np.abs(P.B - B_ext)) / np.max(np.abs(B_ext)))
+    assert g_err <= 1e-14, g_err
+    assert b_err <= 1e-14, b_err
 
 
 def test_relative_nodes_are_nodes_minus_element_origin(oracle_mod):

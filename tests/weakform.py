@@ -110,3 +110,43 @@ def dense_stiffness(nx, ny, nz, N, verts, xi, w):
                 A[np.ix_(g, g)] += K
                 e += 1
     return A, ids
+
+
+def geometry_extended(verts, nx, ny, nz, xi, w):
+    """G [nL, 6] and B [nL] of every local node in extended precision.
+
+    The Jacobian is the analytic derivative of the trilinear vertex map (no
+    derivative matrix, no nodal coordinates), evaluated in ``np.longdouble``
+    (64-bit significand on x86, IEEE quad on Arm) from the FP64 vertices; the
+    inverse is the adjugate over the determinant.  The result carries ~11 more
+    bits than an FP64 evaluation, so it measures the FP64 geometry's rounding.
+    """
+    Lg = np.longdouble
+    n = len(xi)
+    xi = np.asarray(xi).astype(Lg)
+    w = np.asarray(w).astype(Lg)
+    V = np.asarray(verts).astype(Lg).reshape(nz + 1, ny + 1, nx + 1, 3)
+    hf = np.stack([(1 - xi) / 2, (1 + xi) / 2])                 # hat functions [a, node]
+    dh = np.stack([np.full(n, Lg(-0.5)), np.full(n, Lg(0.5))])  # their derivatives
+    J = np.zeros((nz, ny, nx, n, n, n, 3, 3), dtype=Lg)          # [..., k, j, i, x_d, r_b]
+    for c in range(2):
+        for b in range(2):
+            for a in range(2):
+                Vc = V[c:c + nz, b:b + ny, a:a + nx][:, :, :, None, None, None, :]
+                for col, f in enumerate((np.einsum("k,j,i->kji", hf[c], hf[b], dh[a]),
+                                         np.einsum("k,j,i->kji", hf[c], dh[b], hf[a]),
+                                         np.einsum("k,j,i->kji", dh[c], hf[b], hf[a]))):
+                    J[..., :, col] += Vc * f[None, None, None, :, :, :, None]
+    cof = np.empty_like(J)
+    for r in range(3):
+        for s in range(3):
+            r1, r2 = [q for q in range(3) if q != r]
+            s1, s2 = [q for q in range(3) if q != s]
+            sign = 1 if (r + s) % 2 == 0 else -1
+            cof[..., r, s] = sign * (J[..., r1, s1] * J[..., r2, s2] - J[..., r1, s2] * J[..., r2, s1])
+    det = np.einsum("...b,...b->...", J[..., 0, :], cof[..., 0, :])
+    Jinv = np.swapaxes(cof, -1, -2) / det[..., None, None]
+    W = np.einsum("k,j,i->kji", w, w, w)[None, None, None]
+    M = np.einsum("...ab,...cb->...ac", Jinv, Jinv) * (W * det)[..., None, None]
+    G = np.stack([M[..., 0, 0], M[..., 0, 1], M[..., 0, 2], M[..., 1, 1], M[..., 1, 2], M[..., 2, 2]], -1)
+    return G.reshape(-1, 6), (W * det).reshape(-1)
