@@ -235,8 +235,14 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               kept on the device until fetched).
  *   "serve_result" server, ticket, [x: HOST or device double[nL]], OUT state,
  *               OUT iters, OUT rel_res, OUT latency_ms
- *               state 0 queued, 1 active, 2 done; when done, x receives the
- *               solution and the request is released.
+ *               state 0 queued, 1 active, 2 done, 3 failed; when done, x
+ *               receives the solution and the request is released; when
+ *               failed (its problem could not be built, e.g. SEM_EMESH for an
+ *               inverted element), iters holds the error code, rel_res is NaN,
+ *               x is untouched and the request is released.  A failed request
+ *               is drained like a finished one and never stops the others.
+ *               A finished result's device memory counts against the HBM
+ *               budget until it is fetched.
  *   "serve_now" server, OUT seconds       the server clock
  *   "serve_drain" server, tickets (HOST int64[cap]), cap, OUT n
  *               tickets completed since the last drain (at most cap)

@@ -173,6 +173,14 @@ def gid(nx, ny, nz, N):
     return g, b
 
 
+def weighted_dot(c, u, v):
+    """sum_l c_l u_l v_l in ascending l (FP64); c=None means unit weights."""
+    lib = _load()
+    u = _f64(u)
+    c = np.ones_like(u) if c is None else _f64(c)
+    return lib.orc_dot(u.size, _p(c), _p(u), _p(_f64(v)))
+
+
 class Problem:
     """One box-mesh Poisson problem, every quantity computed by the oracle.
 

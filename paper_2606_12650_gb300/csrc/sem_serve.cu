@@ -13,12 +13,15 @@
 // kept there until the client fetches it, and the problem's memory is freed.
 // Latency is measured from the request's arrival time to the end of the round
 // in which it finished, on the server's steady clock.  A request's result
-// does not depend on which other requests shared its rounds.
+// does not depend on which other requests shared its rounds.  A request whose
+// problem cannot be built (an inverted element: SEM_EMESH) fails alone: it
+// leaves the queue with state 3 and its error code, and the others go on.
 #include <cuda_runtime.h>
 
 #include <chrono>
 #include <algorithm>
 #include <deque>
+#include <limits>
 #include <map>
 #include <vector>
 
@@ -37,8 +40,10 @@ struct ServeReq {
     Problem *P = nullptr;
     double *b_dev = nullptr;
     double *x_dev = nullptr;          // result, device-resident until fetched
-    size_t bytes = 0;                 // device bytes held while active
-    int state = 0;                    // 0 queued, 1 active, 2 done
+    size_t bytes = 0;                 // device bytes held while active (and its result until fetched)
+    bool fresh = false;               // admitted, not yet started by the batch engine
+    int err = 0;                      // state 3: the error code of its failed admission
+    int state = 0;                    // 0 queued, 1 active, 2 done, 3 failed
     double t_done = 0.0;
     int64_t iters = 0;
     double res = 0.0;
@@ -64,15 +69,21 @@ double serve_now(const Server *S) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - S->t0).count();
 }
 
-// Device bytes a request will hold while active (problem data + right-hand
-// side), from the node count: FP64 geometry (48), mass (8), CG vectors (32),
-// right-hand side (8) per node, plus for mixed precision BF16/FP32 factors
-// (12 or 24) and FP32 inner vectors (16).
-static size_t request_bytes(int mode, int64_t nL) {
-    size_t per = 48 + 8 + 32 + 8;
+// Device bytes a request holds from admission until its result is fetched,
+// from the node count: FP64 geometry (48), mass (8), CG vectors (32),
+// right-hand side (8) and the retired result (8) per node, plus for mixed
+// precision BF16/FP32 factors (12 or 24) and FP32 inner vectors (16); and per
+// problem its reduction partials, two CG states and the vertex copy, plus
+// 64 KB of allocation granularity.
+static size_t request_bytes(int mode, int64_t nL, int64_t n_verts) {
+    size_t per = 48 + 8 + 32 + 8 + 8;
     if (mode == 1) per += 12 + 16;
     if (mode == 2) per += 24 + 16;
-    return size_t(nL) * per + (size_t(1) << 20);
+    return size_t(nL) * per + kPartialsBytes + 2 * sizeof(CgState) + size_t(n_verts) * 3 * sizeof(double) +
+           (size_t(1) << 16);
+}
+static size_t request_bytes(int mode, const ServeReq *q) {
+    return request_bytes(mode, q->nL, int64_t(q->nx + 1) * (q->ny + 1) * (q->nz + 1));
 }
 
 int serve_open(int capacity, double budget_gb, int mode, double tol, double inner_tol, int K, int maxit,
@@ -99,7 +110,7 @@ int serve_submit(Server *S, int nx, int ny, int nz, int N, const double *verts, 
     if (N < 1 || N > kMaxQ - 1) return set_error(SEM_EARG, "serve_submit: N must be in [1, 9]");
     const int64_t nL = int64_t(nx) * ny * nz * (N + 1) * (N + 1) * (N + 1);
     if (nL >= (int64_t(1) << 31) - 1) return set_error(SEM_ERANGE, "serve_submit: problem too large");
-    if (request_bytes(S->mode, nL) > S->budget)
+    if (request_bytes(S->mode, nL, int64_t(nx + 1) * (ny + 1) * (nz + 1)) > S->budget)
         return set_error(SEM_ENOMEM, "serve_submit: the request alone exceeds the server's HBM budget");
     ServeReq *q = new ServeReq();
     q->ticket = S->next_ticket++;
@@ -179,7 +190,8 @@ static int admit(Server *S, ServeReq *q) {
     std::vector<double>().swap(q->verts);
     std::vector<double>().swap(q->b);
     q->state = 1;
-    q->bytes = request_bytes(S->mode, q->nL);
+    q->fresh = true;
+    q->bytes = request_bytes(S->mode, q);
     S->in_use += q->bytes;
     return SEM_OK;
 }
@@ -187,27 +199,42 @@ static int admit(Server *S, ServeReq *q) {
 int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_completed) {
     int rc = SEM_OK;
     // (1) admission in arrival order, within the slot and HBM limits
-    std::vector<uint8_t> start(S->active.size(), 0);
     while (!S->queue.empty() && int(S->active.size()) < S->capacity) {
         ServeReq *q = S->queue.front();
-        if (S->in_use + request_bytes(S->mode, q->nL) > S->budget) break;
+        if (S->in_use + request_bytes(S->mode, q) > S->budget) break;
         rc = admit(S, q);
+        if (rc == SEM_ENOMEM && !S->active.empty()) break;   // retry once active solves free memory
+        if (rc == SEM_EMESH || rc == SEM_EARG || rc == SEM_ENOMEM) {
+            // the request itself cannot be served: it fails alone
+            S->queue.pop_front();
+            std::vector<double>().swap(q->verts);
+            std::vector<double>().swap(q->b);
+            q->state = 3;
+            q->err = rc;
+            q->t_done = serve_now(S);
+            ++S->completed;
+            S->finished.push_back(q->ticket);
+            continue;
+        }
         if (rc != SEM_OK) return rc;
         S->queue.pop_front();
         S->active.push_back(q);
-        start.push_back(1);
         S->changed = true;
     }
-    // (2) hand the membership to the batch engine
+    // (2) hand the membership to the batch engine; requests admitted since
+    // the last successful hand-over start, the others keep their state
     if (S->changed) {
         std::vector<Problem *> ps;
         std::vector<const double *> bs;
+        std::vector<uint8_t> start;
         for (ServeReq *q : S->active) {
             ps.push_back(q->P);
             bs.push_back(q->b_dev);
+            start.push_back(q->fresh ? 1 : 0);
         }
         rc = batch_set(S->B, ps.data(), bs.data(), start.data(), int(ps.size()));
         if (rc != SEM_OK) return rc;
+        for (ServeReq *q : S->active) q->fresh = false;
         S->changed = false;
     }
     // (3) one round for every active solve
@@ -240,8 +267,7 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         for (size_t k = 0; k < S->active.size(); ++k) {
             ServeReq *q = S->active[k];
             if (gone[k]) {
-                release_active(q);
-                S->in_use -= q->bytes;
+                release_active(q);   // q->bytes stay counted until the result is fetched
                 q->state = 2;
                 ++S->completed;
                 S->finished.push_back(q->ticket);
@@ -258,13 +284,22 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
     return SEM_OK;
 }
 
-// state: 0 queued, 1 active, 2 done (x written, request released).
+// state: 0 queued, 1 active, 2 done (x written, request released), 3 failed
+// (iters = its error code, rel_res = NaN; request released).
 int serve_result(Server *S, int64_t ticket, double *x_out, bool x_on_device, int64_t *state, int64_t *iters,
                  double *rel_res, double *latency_ms) {
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return set_error(SEM_EHANDLE, "serve_result: unknown ticket");
     ServeReq *q = it->second;
     *state = q->state;
+    if (q->state == 3) {
+        *iters = q->err;
+        *rel_res = std::numeric_limits<double>::quiet_NaN();
+        *latency_ms = 1e3 * (q->t_done - q->arrival);
+        S->reqs.erase(it);
+        delete q;
+        return SEM_OK;
+    }
     if (q->state != 2) return SEM_OK;
     if (x_out) {
         const int rc = cuda_check(cudaMemcpyAsync(x_out, q->x_dev, sizeof(double) * q->nL,
@@ -278,6 +313,7 @@ int serve_result(Server *S, int64_t ticket, double *x_out, bool x_on_device, int
     *rel_res = q->res;
     *latency_ms = 1e3 * (q->t_done - q->arrival);
     dev_free(q->x_dev);
+    S->in_use -= q->bytes;
     S->reqs.erase(it);
     delete q;
     return SEM_OK;

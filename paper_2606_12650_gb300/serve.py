@@ -30,7 +30,8 @@ def make_requests(count: int, seed: int, e_lo: int = 8, e_hi: int = 8192, orders
 
 def run_stream(server: Server, requests: list[dict], arrivals, collect_x: bool = False) -> dict:
     """Submit requests at their arrival times (seconds from now), serve them
-    all, and return per-request latency, iterations and residuals."""
+    all, and return per-request latency, iterations and residuals (state 2:
+    solved; 3: failed, iterations then hold the error code)."""
     n = len(requests)
     t0 = server.now()
     tick_of, done, xs = {}, {}, {}
@@ -50,7 +51,7 @@ def run_stream(server: Server, requests: list[dict], arrivals, collect_x: bool =
             k = tick_of[tk]
             x = np.empty(requests[k]["nL"]) if collect_x else None
             st, it, res, lat = server.result(tk, x)
-            done[k] = (lat, it, res)
+            done[k] = (lat, it, res, st)
             if collect_x:
                 xs[k] = x
         if queued == 0 and active == 0 and i < n:
@@ -60,6 +61,7 @@ def run_stream(server: Server, requests: list[dict], arrivals, collect_x: bool =
     last_done = max(float(arrivals[k]) + lat[k] / 1e3 for k in range(n)) if n else 0.0
     return {"latency_ms": lat, "iters": np.array([done[k][1] for k in range(n)]),
             "rel_res": np.array([done[k][2] for k in range(n)]), "x": xs,
+            "state": np.array([done[k][3] for k in range(n)]),
             "span_s": last_done - first, "mean_depth": float(np.mean(depth)) if depth else 0.0}
 
 
