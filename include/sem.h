@@ -181,7 +181,11 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   even-odd split of D; elements per block epb chosen at launch), 2
  *   "persistent" (TMA-pipelined columns, FP32 only), 3 "lines" with the
  *   geometric factors loaded into registers ahead of use (BF16 factors only),
- *   4 "lines" with the factors copied into shared memory with the slab (FP32).  The variant in use is
+ *   4 "lines" with the factors copied into shared memory with the slab
+ *   (FP32), 5 "lines" of the FP64 operator evaluated in double-word FP32
+ *   arithmetic (pairs of FP32 numbers, ~48 significant bits; FP64 inputs,
+ *   outputs and CG recurrences; FP64 only; its factors, a second 48-byte
+ *   per node copy of G, are made on first use).  The variant in use is
  *   kept per kind (0 FP64, 1 FP32 with FP32 G, 2 FP32 with BF16 G) and per N;
  *   the paper's runtime specialises kernels on N and its scripts pick the
  *   thread layout (Section VIII-B); here the choice is made by timing.

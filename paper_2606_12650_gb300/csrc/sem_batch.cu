@@ -780,7 +780,9 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         // item holds several passes (~kAxItemNodes local nodes)
         const int full = kBatchThreads / (P->nq * P->nq);
         const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
-        const bool lines = c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged;
+        // (the double-word FP64 variant runs the FP64 line body here)
+        const bool lines = c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged ||
+                           c.variant == kAxLinesDW;
         const int group = full;
         const int np = P->nq * P->nq * P->nq;
         const int per_item = group * std::max(1, kAxItemNodes / (np * group));

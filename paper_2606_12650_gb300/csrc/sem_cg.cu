@@ -223,7 +223,8 @@ int cg_solve(Problem *P, const double *b, double *x, double tol, int maxit, doub
         cudaGraphExecDestroy(P->graph);
         P->graph = nullptr;
     }
-    rc = capture_graph(P);
+    rc = prepare_f64_variant(P);
+    if (rc == SEM_OK) rc = capture_graph(P);
     if (rc != SEM_OK) return rc;
     // at most ceil(maxit / K) replays; the flag stops earlier replays short
     const int64_t max_replays = (int64_t(maxit) + P->graph_iters - 1) / P->graph_iters;

@@ -100,6 +100,8 @@ struct Problem {
     // FP32 or BF16 ([nL][6]), FP32 inner-CG vectors and the inner CG state
     void *G32 = nullptr;           // float
     void *G16 = nullptr;           // __nv_bfloat16
+    // double-word FP64 operator (allocated on first use): [nL][6] (h, l) FP32 pairs
+    float *Gdw = nullptr;
     float *d32 = nullptr, *r32 = nullptr, *p32 = nullptr, *w32 = nullptr;
     CgState *st_in = nullptr;
     CgState *st_in_host = nullptr;
@@ -118,14 +120,16 @@ enum GPrecision : int { kGF32 = 0, kGBF16 = 1 };
 // block chosen at launch), and the persistent TMA-pipelined column kernel of
 // sem_ax32p.cuh (FP32 only), and the line kernel with the geometric factors
 // loaded into registers before the slab wait (FP32 with BF16 factors only) or
-// staged in shared memory with the slab (FP32).
+// staged in shared memory with the slab (FP32), and the line kernel of the
+// FP64 operator in double-word FP32 arithmetic (sem_ax_dw.cuh, FP64 only).
 enum AxVariant : int {
     kAxColumns = 0,
     kAxLines = 1,
     kAxPersistent = 2,
     kAxLinesPrefetch = 3,
     kAxLinesStaged = 4,
-    kAxVariants = 5
+    kAxLinesDW = 5,
+    kAxVariants = 6
 };
 // What is tuned: the FP64 operator, and the FP32 operator with FP32 or BF16
 // geometric factors.
@@ -149,6 +153,11 @@ int tune_load(const char *path);
 // line-kernel launchers (sem_ax_lines64.cu, sem_ax_lines32.cu); mode 0: y = A x,
 // 1: CG operator on P's vectors, 2: Jacobi-PCG operator
 int launch_lines64(const Problem *P, const double *x, double *y, int mode, int epb);
+// double-word FP64 operator (sem_ax_dw.cu); needs P->Gdw (dw_prepare, not during a capture)
+int launch_lines_dw(const Problem *P, const double *x, double *y, int mode, int epb);
+int dw_prepare(Problem *P);                   // allocate + fill P->Gdw (once)
+void dw_release(Problem *P);
+int prepare_f64_variant(Problem *P);          // whatever the tuned FP64 variant needs (before a capture)
 // gm: where phase 2 reads the factors (0 global, 1 registers, 2 staged in shared memory)
 int launch_lines32(const Problem *P, const float *x, float *y, int gprec, bool cg, int epb, int gm);
 bool lines_epb_ok(int nq, int epb, size_t elem_bytes, int g_stage_bytes = 0);

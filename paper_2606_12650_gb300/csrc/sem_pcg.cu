@@ -209,6 +209,7 @@ int pcg_solve(Problem *P, const double *b, double *x, double tol, int maxit, dou
                                                             P->st, maxit, tol, hist);
     count_launches(1);
     rc = cuda_check(cudaGetLastError(), "pcg_init_kernel");
+    if (rc == SEM_OK) rc = prepare_f64_variant(P);
     if (rc == SEM_OK) rc = capture_pcg(P);
     if (rc != SEM_OK) return rc;
     const int K = P->nL < (1 << 20) ? 64 : 16;

@@ -443,6 +443,7 @@ void problem_destroy(Problem *P) {
     if (P->graph_pcg) cudaGraphExecDestroy(P->graph_pcg);
     if (P->dinv) dev_free(P->dinv);
     mixed_release(P);
+    dw_release(P);
     double *dptrs[] = {P->verts, P->G, P->B, P->c, P->x, P->r, P->p, P->w, P->partials};
     for (double *q : dptrs)
         if (q) dev_free(q);

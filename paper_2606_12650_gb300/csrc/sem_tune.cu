@@ -5,7 +5,8 @@
 // choose the thread layout.  Here the variants are compiled ahead of time for
 // every order and the choice is made by timing: for one order and one
 // precision, each candidate -- the column kernel, the persistent kernel
-// (FP32), and the line kernel at several element-per-block counts -- runs
+// (FP32), the line kernel at several element-per-block counts, and for FP64
+// the line kernel in double-word FP32 arithmetic -- runs
 // the CG operator `reps` times on a real problem, and the fastest is kept.
 // The table can be saved to and loaded from a text file (one line per entry:
 // kind, N, variant, elements per block, microseconds), so a tuned table is
@@ -67,19 +68,21 @@ bool choice_ok(int kind, int nq, const TuneChoice &c) {
         case kAxLinesPrefetch: return kind == kTuneF32G16 && lines_epb_ok(nq, c.epb, elem_bytes(kind));
         case kAxLinesStaged:
             return kind != kTuneF64 && lines_epb_ok(nq, c.epb, elem_bytes(kind), kind == kTuneF32G32 ? 24 : 12);
+        case kAxLinesDW: return kind == kTuneF64 && lines_epb_ok(nq, c.epb, sizeof(double));
         default: return false;
     }
 }
 
 // The candidates for (kind, nq): the kind's column kernel, then the line
-// kernel with ~64 .. 512 threads per block (and, for BF16 factors, the same
-// with the factors prefetched).
+// kernel with ~64 .. 512 threads per block (for FP64 also in double-word
+// arithmetic; for FP32 with staged factors and, for BF16 factors, with the
+// factors prefetched).
 int candidates(int kind, int nq, TuneChoice *out, int cap) {
     int n = 0;
     out[n++] = {kind == kTuneF64 ? kAxColumns : kAxPersistent, 0, 0.0};
-    // the line kernel, then (FP32) its variants with prefetched or staged factors
-    int variants[3] = {kAxLines, kAxLinesStaged, kAxLinesPrefetch};
-    const int nv = kind == kTuneF64 ? 1 : (kind == kTuneF32G32 ? 2 : 3);
+    const bool f64 = kind == kTuneF64;
+    const int variants[3] = {kAxLines, f64 ? kAxLinesDW : kAxLinesStaged, kAxLinesPrefetch};
+    const int nv = f64 ? 2 : (kind == kTuneF32G32 ? 2 : 3);
     for (int v = 0; v < nv; ++v) {
         int prev = 0;
         for (int t : {64, 128, 192, 256, 384, 512}) {
@@ -148,8 +151,7 @@ int tune_problem(Problem *P, int kind, int reps, double *cand, int cap, int *n_c
     if (reps < 1 || reps > 10000) return set_error(SEM_EARG, "autotune: reps must be in [1, 10000]");
     const int nq = P->nq;
     const int gprec = kind == kTuneF32G32 ? kGF32 : kGBF16;
-    int rc = SEM_OK;
-    if (kind != kTuneF64) rc = mixed_prepare(P, gprec);
+    int rc = kind != kTuneF64 ? mixed_prepare(P, gprec) : dw_prepare(P);
     if (rc != SEM_OK) return rc;
     CgState *st = kind == kTuneF64 ? P->st : P->st_in;
     unsigned blocks = unsigned(std::min<int64_t>((P->nL + 255) / 256, int64_t(sm_count()) * 8));
@@ -207,7 +209,8 @@ int tune_save(const char *path) {
     FILE *f = fopen(path, "w");
     if (!f) return set_error(SEM_EARG, std::string("autotune_save: cannot write ") + path);
     fprintf(f, "# libsem operator table: kind(0 fp64, 1 fp32/fp32 G, 2 fp32/bf16 G) N variant(0 columns, "
-               "1 lines, 2 persistent, 3 lines with G prefetch, 4 lines with G staged) elements_per_block us\n");
+               "1 lines, 2 persistent, 3 lines with G prefetch, 4 lines with G staged, 5 lines in double-word FP32) "
+               "elements_per_block us\n");
     for (int k = 0; k < kTuneKinds; ++k)
         for (int q = 2; q <= kMaxQ; ++q) {
             const TuneChoice &c = g_tab[k][q];

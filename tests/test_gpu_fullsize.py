@@ -93,6 +93,41 @@ def test_fullsize_cg_history(full, oracle_full):
     np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=0)
 
 
+def test_fullsize_double_word_operator(full, oracle_full):
+    """The double-word FP64 operator at full size, whatever the tuner chose:
+    whole-vector operator within 1e-13 of the oracle, the first 5 CG
+    residuals within rtol 1e-9, the solve to 1e-8 with the oracle's
+    operator."""
+    from paper_2606_12650_gb300 import sem
+    M, _ = full
+    P = oracle_full
+    saved = sem.autotune_get(0, N)
+    try:
+        sem.autotune_set(0, N, 5, saved[1] if saved[0] == 5 else 4)
+        x = normal_field(M.nL, 4)
+        xd = torch.from_numpy(x).cuda()
+        yd = torch.full_like(xd, float("nan"))
+        M.ax(xd, yd)
+        torch.cuda.synchronize()
+        y_ref = P.ax_local(x)
+        assert np.abs(yd.cpu().numpy() - y_ref).max() / np.abs(y_ref).max() < 1e-13
+        del xd, yd
+        b_ref = P.mask(P.gs(normal_field(P.nL, 3)))
+        _, _, h_ref = P.cg(b_ref, maxit=5, tol=0.0)
+        b = torch.from_numpy(b_ref).cuda()
+        x = torch.empty_like(b)
+        hist = torch.zeros(6, dtype=torch.float64, device="cuda")
+        assert M.cg_solve(b, x, 0.0, 5, hist)[0] == 5
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=0)
+        it, rel = M.cg_solve(b, x, 1e-8, 100000)
+        torch.cuda.synchronize()
+        assert rel <= 1e-8
+        assert P.true_residual(b_ref, x.cpu().numpy()) <= 1.5e-8
+    finally:
+        sem.autotune_set(0, N, saved[0], saved[1])
+
+
 def test_fullsize_solves_meet_tolerance(full, oracle_full):
     M, _ = full
     P = oracle_full

@@ -6,7 +6,10 @@ norm) of the oracle for every order, including odd N+1 (a middle node in the
 even-odd split) and blocks whose last element group is ragged; CG and
 Jacobi-PCG residual histories within rtol 1e-9 of the oracle's; FP32
 operator within 5e-5 of the oracle evaluated on the same rounded geometric
-factors.  The tuner returns one timing per candidate, keeps the fastest, and
+factors.  The double-word variant (the FP64 operator in pairs of FP32
+numbers, ~48 significant bits) is held to the same FP64 bars; its CG
+histories get the absolute floor scaled to its rounding unit (2^-48 instead
+of 2^-53 of ||b||).  The tuner returns one timing per candidate, keeps the fastest, and
 its table survives a save/load round trip; changing the variant makes
 captured CG graphs be captured again.
 """
@@ -20,7 +23,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 F64, F32G32, F32G16 = 0, 1, 2
-COLUMNS, LINES, PERSISTENT, LINES_PF, LINES_ST = 0, 1, 2, 3, 4
+COLUMNS, LINES, PERSISTENT, LINES_PF, LINES_ST, LINES_DW = 0, 1, 2, 3, 4, 5
 
 
 def bf16_round(a):
@@ -63,7 +66,8 @@ def test_f64_ax_parity_every_variant(semlib, oracle_mod, N):
     y_ref, yg_ref = P.ax_local(x), P.apply(x)
     xd = torch.from_numpy(x).cuda()
     nq2 = (N + 1) ** 2
-    choices = [(COLUMNS, 0)] + [(LINES, e) for e in sorted({1, 2, 3, max(1, 256 // nq2), max(1, 512 // nq2)})]
+    epbs = sorted({1, 2, 3, max(1, 256 // nq2), max(1, 512 // nq2)})
+    choices = [(COLUMNS, 0)] + [(LINES, e) for e in epbs] + [(LINES_DW, e) for e in epbs]
     for v, epb in choices:
         with variant(F64, N, v, epb):
             yd = torch.full_like(xd, float("nan"))
@@ -76,7 +80,9 @@ def test_f64_ax_parity_every_variant(semlib, oracle_mod, N):
 
 
 @pytest.mark.parametrize("N,v,epb", [(7, LINES, 1), (7, LINES, 2), (7, LINES, 4), (4, LINES, 3), (8, LINES, 2),
-                                     (3, LINES, 8), (7, COLUMNS, 0), (4, COLUMNS, 0)])
+                                     (3, LINES, 8), (7, COLUMNS, 0), (4, COLUMNS, 0), (7, LINES_DW, 1),
+                                     (7, LINES_DW, 2), (7, LINES_DW, 4), (4, LINES_DW, 3), (8, LINES_DW, 2),
+                                     (3, LINES_DW, 8), (6, LINES_DW, 2)])
 def test_cg_history_every_variant(semlib, oracle_mod, N, v, epb):
     P, M = _pair(oracle_mod, 4, 4, 4, N, seed=1)
     b_ref = P.rhs_sin()
@@ -88,20 +94,23 @@ def test_cg_history_every_variant(semlib, oracle_mod, N, v, epb):
         it, _ = M.cg_solve(b, x, 0.0, 100, hist)
     assert it == 100 == it_ref
     # rtol 1e-9 while the residual is large; the operators' rounding (~1e-16
-    # of ||b||) stays an absolute floor once CG has reduced it by ~1e9 (N <= 4)
-    np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=1e-14 * h_ref[0])
+    # of ||b||, ~3e-15 in double-word) stays an absolute floor once CG has
+    # reduced it by ~1e9 (N <= 4)
+    floor = (3e-13 if v == LINES_DW else 1e-14) * h_ref[0]
+    np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=floor)
     assert _rel(x.cpu().numpy(), x_ref) < 1e-10
     M.free()
 
 
-def test_lines_pcg_history(semlib, oracle_mod):
+@pytest.mark.parametrize("v", [LINES, LINES_DW])
+def test_lines_pcg_history(semlib, oracle_mod, v):
     P, M = _pair(oracle_mod, 4, 4, 4, 7, seed=1)
     b_ref = P.rhs_sin()
     x_ref, it_ref, h_ref = P.pcg(b_ref, maxit=60, tol=0.0)
     b = torch.from_numpy(b_ref).cuda()
     x = torch.empty_like(b)
     hist = torch.zeros(61, dtype=torch.float64, device="cuda")
-    with variant(F64, 7, LINES, 2):
+    with variant(F64, 7, v, 2):
         it, _ = M.pcg_solve(b, x, 0.0, 60, hist)
     assert it == 60 == it_ref
     np.testing.assert_allclose(hist.cpu().numpy(), h_ref, rtol=1e-9, atol=0)
@@ -176,7 +185,7 @@ def test_autotune_keeps_fastest_and_round_trips(semlib, oracle_mod, tmp_path):
             cands = M.autotune(kind, reps=3)
             assert len(cands) >= 3
             assert cands[0][0] == (COLUMNS if kind == F64 else PERSISTENT)
-            allowed = {F64: (LINES,), F32G32: (LINES, LINES_ST), F32G16: (LINES, LINES_ST, LINES_PF)}[kind]
+            allowed = {F64: (LINES, LINES_DW), F32G32: (LINES, LINES_ST), F32G16: (LINES, LINES_ST, LINES_PF)}[kind]
             assert all(c[0] in allowed and c[1] >= 1 for c in cands[1:])
             assert all(c[2] > 0 for c in cands)
             best = min(cands, key=lambda c: c[2])
@@ -192,6 +201,8 @@ def test_autotune_keeps_fastest_and_round_trips(semlib, oracle_mod, tmp_path):
             sem.autotune_set(F32G32, 7, LINES_PF, 4)
         with pytest.raises(sem.SemError):        # staged factors are for FP32 arithmetic only
             sem.autotune_set(F64, 7, LINES_ST, 4)
+        with pytest.raises(sem.SemError):        # double-word arithmetic is the FP64 operator's
+            sem.autotune_set(F32G32, 7, LINES_DW, 4)
         sem.autotune_load(str(path))
         for k in (F64, F32G32, F32G16):
             v, e, us = sem.autotune_get(k, 7)
