@@ -20,9 +20,10 @@
 //     set-up into a [nL][6] (h, l) array of the same 48 bytes per node as FP64.
 // Each value carries ~48 significant bits: the operator matches the FP64
 // direct evaluation to ~2e-14 of max|y| on random input (FP64: ~6e-16), well
-// inside the 1e-13 parity bar, for inputs within FP32's exponent range
-// (|v| in [2^-78, 2^127] keeps the low parts normal).  Why: GB300 executes
-// FP64 at 1/64 of its FP32 rate, and the FP64 line kernel is bound by its
+// inside the 1e-13 parity bar, for inputs whose magnitudes lie within FP32's
+// exponent range with room for the low part (~[2^-100, 2^126]: below it the
+// low parts become subnormal and precision falls towards FP32's).
+// Why: GB300 executes FP64 at 1/64 of its FP32 rate, and the FP64 line kernel is bound by its
 // ~50 DFMA per node; here a node costs ~450 FP32 operations (~7 DFMA worth),
 // which moves the bound from the FP64 pipe towards HBM bandwidth.
 #pragma once
@@ -36,13 +37,47 @@ struct alignas(8) dwf {
     float h, l;
 };
 
-// h = rn(d); d - h is exact in FP64 and rounded once more to FP32.
+// FP64 <-> double-word conversions in integer and FP32 arithmetic: GB300
+// runs FP64 conversions on its FP64 pipe (1/64 rate), where a handful per
+// node would cost as much as the double-word arithmetic itself.
+//
+// d -> (h, l): h = d rounded to 24 significant bits (half away from zero: a
+// 2^28 carry into the 52-bit significand, then truncation), re-biased from
+// the FP64 to the FP32 exponent; the remainder d - h is an exact signed
+// 29-bit multiple m of d's last significand place 2^(e-1075); m is widened
+// to FP32 exactly in two halves (float(k) = bits(2^23 + k) - 2^23, exact for
+// |k| < 2^22) joined by one FMA (so l = rn(m) 2^(e-1075)), scaled by two
+// powers of two (each representable for 2^-126 <= |d|), and given d's sign.
+// |d| < 2^-126 (and zero) gives (+-0, 0); |d| >= 2^128 is outside the range.
 __device__ __forceinline__ dwf dw_from_double(double d) {
-    const float h = __double2float_rn(d);
-    return {h, __double2float_rn(d - double(h))};
+    const uint64_t bits = uint64_t(__double_as_longlong(d));
+    const uint32_t hi = uint32_t(bits >> 32);
+    const uint32_t sign = hi & 0x80000000u;
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    const uint64_t rb = bits + (uint64_t(1) << 28);
+    const uint32_t hb = ((uint32_t(rb >> 29) - (384u << 23)) & 0x7fffffffu) | sign;
+    const int32_t m = int32_t(uint32_t(rb) & 0x1fffffffu) - 0x10000000;
+    const float fmh = __fsub_rn(__uint_as_float(0x4b400000u + uint32_t(m >> 14)), 12582912.0f);
+    const float fml = __fsub_rn(__uint_as_float(0x4b000000u | (uint32_t(m) & 0x3fffu)), 8388608.0f);
+    const float fm = __fmaf_rn(fmh, 16384.0f, fml);
+    const float l = __fmul_rn(__fmul_rn(fm, 0x1p-52f), __uint_as_float((e - 896u) << 23));
+    if (e < 897u) return {__uint_as_float(sign), 0.0f};
+    return {__uint_as_float(hb), __uint_as_float(__float_as_uint(l) ^ sign)};
 }
 
-__device__ __forceinline__ double dw_to_double(dwf v) { return double(v.h) + double(v.l); }
+// Exact FP32 -> FP64 widening by re-biasing the exponent; zero and
+// subnormal FP32 inputs (|f| < 2^-126) give a signed zero.
+__device__ __forceinline__ double widen_f32(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t s = b & 0x80000000u;
+    const bool normal = (b & 0x7f800000u) != 0u;
+    const uint32_t hi = normal ? (s | (((b & 0x7fffffffu) >> 3) + (896u << 20))) : s;
+    const uint32_t lo = normal ? (b << 29) : 0u;
+    return __hiloint2double(int(hi), int(lo));
+}
+
+// h + l rounded once to FP64 (one FP64 addition).
+__device__ __forceinline__ double dw_to_double(dwf v) { return widen_f32(v.h) + widen_f32(v.l); }
 
 // s + e = a + b exactly (Knuth's TwoSum: no ordering of |a|, |b| needed).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -202,7 +237,8 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
     const int tp = b * P1 + a;
 
     // ---- (0b) the thread's t line: CG prologue in FP64, then to double-word
-    // in place (each node is converted by the one thread that owns its t line)
+    // in place (each node is converted by the one thread that owns its t line;
+    // the converted slab is read again for <p, y> in phase 4)
     dwf xk[NQ];
     double *slab = CG ? s2 : s1;
     dwf *SXw = reinterpret_cast<dwf *>(slab);
@@ -302,7 +338,7 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
             const int pq = k * P2 + tp;
             const dwf yv = dw_add(dw_add(SU[pq], SV[pq]), yt[k]);
             y[nb + k * NQ2 + tq] = dw_to_double(yv);
-            if (CG) acc = dw_fma(xk[k], yv, acc);
+            if (CG) acc = dw_fma(SX[k * NQ2 + tq], yv, acc);
         }
     }
     if (CG) *part = dw_to_double(acc);
