@@ -14,7 +14,9 @@ Also reported on the same JSON line:
   e2e           the same metric through the public API with host buffers
                 (pinned b copied in and x copied out every step)
   roofline      the dominant kernel (the fused CG operator kernel) timed with
-                CUDA events on libsem's stream, against the FP64 pipe peak
+                CUDA events on libsem's stream: against HBM bandwidth when the
+                tuner picked the double-word operator (FP64 values evaluated
+                in FP32 pairs), against the FP64 pipe for the DFMA kernels
   mixed         the same solve by mixed-precision iterative refinement (FP32
                 inner CG, BF16 geometric factors, FP64 outer residual), with
                 its own HBM roofline, solves/s against FP64, and a 1e-10 leg
@@ -26,6 +28,10 @@ Also reported on the same JSON line:
   batched       256 uneven problems, each CG phase one persistent launch
   serve         Poisson arrivals at 100..5000 req/s: p50/p99 latency, solves/s
   paper_sweep   the paper's protocol: GDOF/s against E = 2^1..2^14, N = 4, 6, 8
+  vs_oracle     the small workload (E = 64, N = 7, sine source) solved on the
+                GPU in FP64 and mixed precision to 1e-8 and 1e-10, each error
+                stated against the oracle's stored solution (tol 1e-12)
+  summary       the headline figures of every leg, last on the line
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 Multi-GPU (torchrun): every rank solves an independent problem (replicas,
@@ -53,16 +59,19 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
               for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
-                        "sem_internal.h")]
+                        "sem_internal.h", "sem_ax_dw.cuh", "sem_ax_dw.cu")]
+GOLDEN_SMALL = os.path.join(ROOT, "tests", "golden", "oracle_cg_E64_N7.npz")
 AX32_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
                 for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax32.cu", "sem_ax_lines32.cu", "sem_ax32p.cuh",
                           "sem_device.cuh", "sem_internal.h")]
-VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch", 4: "lines_staged"}
+VARIANTS = {0: "columns", 1: "lines", 2: "persistent", 3: "lines_prefetch", 4: "lines_staged", 5: "lines_dw"}
 
 
 def kernel_label(variant, epb, N, t, gt):
     """Name of the CG-operator kernel the tuner chose."""
     q = N + 1
+    if variant == 5:
+        return f"ax_dw_kernel<{q},CG> ({epb} elements/block, FP64 in double-word FP32 arithmetic)"
     if variant in (1, 3, 4):
         pf = {1: "", 3: ", G prefetched", 4: ", G staged"}[variant]
         return f"ax_lines_kernel<{q},{t},{gt},CG> ({epb} elements/block{pf})"
@@ -391,17 +400,34 @@ def run_ours(a):
     except (OSError, ValueError):
         pass
     v64, e64, _ = sem.autotune_get(sem.TUNE_F64, N)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
-                "kernel": kernel_label(v64, e64, N, "double", "double"), "launch_ms": ax_ms,
-                "flops_note": "achieved counts the operator's direct-evaluation flops, 12(N+1)^4 + 15(N+1)^3 per "
-                              "element; the line kernel's even-odd split executes fewer (48 instead of 64 "
-                              "operations per 1d line at N = 7)",
-                "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
-                "hbm_gbs_at_alg_bytes": bytes_alg / (ax_ms * 1e-3) / 1e9,
-                "fp64_probe_gflops": fp64.value / 1e9,
-                "peak_note": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 2 DFMA/clk x "
-                             "2 flop x 2.07 GHz); fp64_probe_gflops is the same pipe measured live"}
+    hbm, hbm_how = hbm_peak()
+    gbs = bytes_alg / (ax_ms * 1e-3) / 1e9
+    if v64 == 5:
+        # double-word arithmetic on the FP32 pipe: the FP64 pipe no longer
+        # bounds the kernel; HBM bandwidth is its roofline
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "traffic": traffic, "kernel": kernel_label(v64, e64, N, "double", "double"),
+                    "launch_ms": ax_ms, "alg_bytes_per_launch": bytes_alg,
+                    "alg_bytes_note": "96 B per local node: r, p, x read; p, w, x written (x: the deferred "
+                                      "update); 6 geometric factors of 8 B (FP64, or their double-word FP32 "
+                                      "pairs, the same 48 B)",
+                    "peak_source": hbm_how,
+                    "fp64_equiv_gflops": achieved, "fp64_pipe_peak_gflops": FP64_PEAK_GFLOPS,
+                    "fp64_equiv_note": "the operator's direct-evaluation flops, 12(N+1)^4 + 15(N+1)^3 per "
+                                       "element, per second: above the FP64 pipe's peak because the kernel "
+                                       "computes in FP32 pairs (~48-bit significands) on the FP32 pipe"}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+                    "kernel": kernel_label(v64, e64, N, "double", "double"), "launch_ms": ax_ms,
+                    "flops_note": "achieved counts the operator's direct-evaluation flops, 12(N+1)^4 + "
+                                  "15(N+1)^3 per element; the line kernel's even-odd split executes fewer (48 "
+                                  "instead of 64 operations per 1d line at N = 7)",
+                    "flops_per_launch": flops, "alg_bytes_per_launch": bytes_alg,
+                    "hbm_gbs_at_alg_bytes": gbs, "hbm_frac_at_alg_bytes": gbs / hbm,
+                    "peak_note": "FP64 pipe from unit counts and the maximum SM clock (152 SMs x 2 DFMA/clk x "
+                                 "2 flop x 2.07 GHz); fp64_probe_gflops is the same pipe measured live"}
+    roofline["fp64_probe_gflops"] = fp64.value / 1e9
 
     # ---- Jacobi-preconditioned CG (FP64), the original Nekbone method
     pcg = None
@@ -444,12 +470,17 @@ def run_ours(a):
         served = {"workload": f"Poisson arrivals, {a.serve_requests} requests per rate, E log-uniform [8, 8192] "
                               f"(near-cubic boxes), N in {{5,7}}, jitter 5%, random source, tol {a.tol:g}, "
                               "mixed precision (BF16 G), 40 GB admission budget, 8 CG iterations per round",
-                  "rates": rows}
+                  "rates": rows, "closed_loop": run_served_ceiling(a, stream, sem, torch)}
 
     # ---- the paper's own protocol: GDOF/s against E for N = 4, 6, 8
     sweep_paper = None
     if not a.no_paper_sweep and rank == 0:
         sweep_paper = run_paper_sweep(a, stream, sem, torch)
+
+    # ---- errors against the FP64 oracle on the small workload
+    vs_oracle = None
+    if rank == 0:
+        vs_oracle = run_vs_oracle(a, sem, torch)
 
     # ---- end to end through the public API, host buffers
     e2e = None
@@ -499,22 +530,94 @@ def run_ours(a):
                               f"started together, time of the slowest: {t_rep[0]:.1f} s)"}
 
     if rank == 0:
+        # long tables first; the headline figures of every leg last (the
+        # tail of the line is what survives truncated records)
         line = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": t_max / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "dtype_note": ("FP64 vectors, recurrences and reductions; the operator kernel the tuner chose "
+                               + ("evaluates in double-word FP32 (~48-bit significands)" if v64 == 5
+                                  else "evaluates in FP64")),
                 "config": config_of(a, world, iters_total // max(a.steps, 1)),
+                "autotune": tune, "paper_sweep": sweep_paper, "batched": batched, "serve": served,
+                "pcg": pcg, "mixed": mixed, "vs_oracle": vs_oracle,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                "pcg": pcg, "mixed": mixed, "batched": batched, "serve": served, "autotune": tune,
-                "paper_sweep": sweep_paper,
                 "clocks": clk.summary(),
                 "result": {"rel_res_recursive": rel, "rel_res_true": true_res,
-                           "cg_iters_per_solve": iters_total // max(a.steps, 1)}}
+                           "cg_iters_per_solve": iters_total // max(a.steps, 1)},
+                "summary": summarize(value, t_max / a.steps, roofline, mixed, batched, served, pcg, vs_oracle)}
         print(json.dumps(line), flush=True)
     M.free()
     torch.cuda.synchronize()
     sem.finalize()
     if world > 1:
         dist.destroy_process_group()
+
+
+def summarize(value, ms_fp64, roofline, mixed, batched, served, pcg, vs_oracle):
+    """The headline figure of every leg in a few keys."""
+    s = {"fp64_gdofs": value, "fp64_ms_per_solve": ms_fp64, "fp64_solves_per_s": 1e3 / ms_fp64,
+         "operator": roofline.get("kernel"), "operator_bound": roofline.get("bound"),
+         "operator_frac": roofline.get("frac")}
+    if mixed:
+        s.update(mixed_gdofs=mixed["value"], mixed_solves_per_s=mixed["solves_per_s"],
+                 mixed_speedup_vs_fp64=mixed["speedup_solves_vs_fp64"], mixed_rel_res_true=mixed["rel_res_true"],
+                 mixed_hbm_frac=mixed["roofline"]["frac"])
+    if vs_oracle:
+        s["err_vs_oracle_E64"] = {k: v["err_vs_oracle_inf"] for k, v in vs_oracle["solves"].items()}
+    if batched:
+        s["batched_solves_per_s"] = {"fp64": batched["fp64"]["solves_per_s"],
+                                     "mixed": batched["mixed_bf16"]["solves_per_s"]}
+    if served:
+        s["served"] = [{"rate": r["rate_req_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                        "solves_per_s": r["solves_per_s"]} for r in served["rates"]]
+        if served.get("closed_loop"):
+            s["served_closed_loop_solves_per_s"] = served["closed_loop"]["solves_per_s"]
+    if pcg:
+        s["pcg_ms_per_solve"] = pcg["ms_per_solve"]
+    return s
+
+
+def run_vs_oracle(a, sem, torch):
+    """The small workload (E = 64, N = 7, jitter seed 1, sine source) solved on
+    the GPU to 1e-8 and 1e-10 -- FP64 CG with the tuned operator, FP64 CG
+    with the DFMA line kernel, mixed refinement with BF16 and FP32 factors --
+    each error stated against the FP64 oracle's solution to 1e-12, which
+    tests/golden/make_oracle_cg.py wrote (bench.py does not run the oracle)."""
+    import numpy as np
+    from paper_2606_12650_gb300 import Mesh
+    from paper_2606_12650_gb300.inputs import box_vertices
+    try:
+        g = np.load(GOLDEN_SMALL)
+    except OSError:
+        return None
+    nx, N = int(g["nx"]), int(g["N"])
+    M = Mesh(nx, nx, nx, N, box_vertices(nx, nx, nx, 0.05, seed=int(g["seed"])))
+    b = torch.from_numpy(g["b"]).cuda()
+    x_ref = g["x"]
+    scale = np.abs(x_ref).max()
+    out = {"workload": f"box {nx}x{nx}x{nx} (E={nx ** 3}), N={N}, jitter 5% seed {int(g['seed'])}, sine source; "
+                       f"oracle CG to {float(g['tol']):g} ({int(g['iters'])} iterations) stored in "
+                       "tests/golden/oracle_cg_E64_N7.npz", "solves": {}}
+    v64, e64, _ = sem.autotune_get(sem.TUNE_F64, N)
+    for tol in (1e-8, 1e-10):
+        legs = [("fp64_tuned", None), ("fp64_dfma_lines", (1, 4)), ("mixed_bf16", 1), ("mixed_fp32", 0)]
+        for name, how in legs:
+            x = torch.empty_like(b)
+            if name.startswith("fp64"):
+                if how is not None:
+                    sem.autotune_set(sem.TUNE_F64, N, *how)
+                it, rel = M.cg_solve(b, x, tol, a.maxit)
+                sem.autotune_set(sem.TUNE_F64, N, v64, e64)
+                info = {"iters": it, "rel_res": rel}
+            else:
+                inner, outer, rel = M.cg_mixed(b, x, tol, 50, a.inner_tol, a.maxit, how)
+                info = {"inner_iters": inner, "outer_iters": outer, "rel_res_true": rel}
+            torch.cuda.synchronize()
+            info["err_vs_oracle_inf"] = float(np.abs(x.cpu().numpy() - x_ref).max() / scale)
+            out["solves"][f"{name}_tol{tol:g}"] = info
+    M.free()
+    return out
 
 
 def hbm_peak():
@@ -659,6 +762,40 @@ def run_batched(a, job, rank, stream, sem, torch):
     for m in meshes:
         m.free()
     return out
+
+
+def run_served_ceiling(a, stream, sem, torch, count=256):
+    """The serving ceiling: `count` requests of the served mix (E log-uniform
+    [8, 8192], N in {5, 7}) all present at once, solved by the batch engine
+    (mixed precision, BF16 factors) closed-loop: no arrivals, no admission."""
+    from paper_2606_12650_gb300 import Batch, Mesh
+    from paper_2606_12650_gb300.serve import make_requests
+    reqs = make_requests(count, seed=5)
+    meshes, bs = [], []
+    for r in reqs:
+        m = Mesh(r["nx"], r["ny"], r["nz"], r["N"], r["verts"])
+        f = torch.from_numpy(r["f"]).cuda()
+        m.gs(f)
+        m.mask(f)
+        meshes.append(m)
+        bs.append(f)
+    B = Batch(meshes)
+    b_all = torch.cat(bs)
+    del bs
+    x_all = torch.empty_like(b_all)
+    B.solve(b_all, x_all, a.tol, a.maxit, 1, a.inner_tol)     # warm-up (graph capture)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its, res = B.solve(b_all, x_all, a.tol, a.maxit, 1, a.inner_tol)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    B.free()
+    for m in meshes:
+        m.free()
+    return {"workload": f"{count} requests of the served mix solved as one batch (mixed, BF16 G), closed loop",
+            "ms": ms, "solves_per_s": 1e3 * count / ms, "max_rel_res": float(res.max())}
 
 
 def run_paper_sweep(a, stream, sem, torch):
