@@ -46,6 +46,7 @@ extern "C" {
 #define SEM_ECUDA      -8  /* CUDA runtime error (message has the CUDA text) */
 #define SEM_EMESH      -9  /* invalid mesh: non-positive Jacobian */
 #define SEM_EHANDLE   -10  /* unknown problem handle */
+#define SEM_ECOMM     -11  /* a sem_comm callback (exchange, allreduce) reported failure */
 
 /* ---- sem_update operations (Section IV, Table "update operations") ------- */
 #define SEM_ALLOC 0  /* allocate the device mirror of host[start, end), no copy  */
@@ -75,6 +76,25 @@ typedef struct sem_arg {
         void *ptr;
     } v;
 } sem_arg;
+
+/* Communication between the ranks of one problem split across processes
+ * ("dist_*" kernels; Nekbone runs its CG under MPI with the elements divided
+ * among ranks, Section VIII-A; the paper names multi-node runs as future
+ * work, Section IX).  libsem calls these on the calling thread with HOST
+ * buffers it owns (pinned); each returns 0 on success, anything else makes
+ * the calling sem_run return SEM_ECOMM.
+ *   allreduce_sum(ctx, vals, n): vals[0..n) <- their sum over all ranks, the
+ *       same bits on every rank.
+ *   exchange(ctx, send_lo, recv_lo, send_hi, recv_hi, n): send n values to
+ *       the rank below (send_lo) / above (send_hi) and receive theirs into
+ *       recv_lo / recv_hi; a NULL pair means there is no such neighbour.
+ * The struct is passed to sem_run as a SEM_ARG_HOST pointer. */
+typedef struct sem_comm {
+    int (*allreduce_sum)(void *ctx, double *vals, int n);
+    int (*exchange)(void *ctx, const double *send_lo, double *recv_lo, const double *send_hi, double *recv_hi,
+                    int64_t n);
+    void *ctx;
+} sem_comm;
 
 /* Device allocator hooks: alloc returns a device pointer (NULL on failure,
  * 256-byte aligned or better); free releases it.  ctx is passed through. */
@@ -251,6 +271,30 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   "serve_drain" server, tickets (HOST int64[cap]), cap, OUT n
  *               tickets completed since the last drain (at most cap)
  *   "serve_close" server
+ *   One problem split across ranks (processes) by whole element layers
+ *   along z (Nekbone's element decomposition under MPI, Section VIII-A):
+ *   "dist_mesh" nx, ny, nz, N, verts (device double[(nx+1)(ny+1)(nz+1)*3]),
+ *               neighbours, OUT handle
+ *               This rank's slab: an nx x ny x nz box of elements whose
+ *               vertex planes are those of the global mesh; neighbours bit 0:
+ *               a rank holds the layers below (the z0 face is an interface,
+ *               not Dirichlet), bit 1: above (z1 face).  The other faces are
+ *               Dirichlet.  Weights use the global multiplicities.
+ *   "dist_info" handle, OUT nL
+ *   "dist_ax"   handle, x, y (device double[nL])   y = A_local x on the slab
+ *   "dist_gs"   handle, u (device double[nL]), comm (HOST sem_comm)
+ *               u <- mask(QQ^T u) of the whole problem: the slab's sum, one
+ *               exchange of the interface-plane partial sums with each
+ *               neighbour (lower rank's partial added first, so both hold the
+ *               same bits), the global Dirichlet mask
+ *   "dist_dot"  handle, u, v, comm, OUT double   the global weighted dot
+ *   "dist_cg_solve" handle, b, x (device double[nL]), tol, maxit, comm,
+ *               hist (HOST double[maxit+1] or NONE), OUT iters, OUT rel_res
+ *               CG of the whole problem, each rank on its slab: the
+ *               operator kernel of cg_solve, the distributed sum above, two
+ *               scalar allreduces per iteration (<p, A p>, <r, r>); b and x
+ *               hold this slab's local nodes; hist[k] = sqrt(<r_k, r_k>)
+ *   "dist_free" handle
  * Unknown names return SEM_EKERNEL; wrong argument counts or kinds SEM_EARG. */
 int sem_run(const char *kernel, int nargs, const sem_arg *args);
 

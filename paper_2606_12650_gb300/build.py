@@ -16,7 +16,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libsem.so")
 SOURCES = ["sem_api.cu", "sem_setup.cu", "sem_ax.cu", "sem_ax32.cu", "sem_ax_lines64.cu", "sem_ax_lines32.cu",
            "sem_ax_dw.cu",
-           "sem_tune.cu", "sem_cg.cu", "sem_pcg.cu", "sem_mixed.cu", "sem_batch.cu", "sem_serve.cu", "sem_probe.cu",
+           "sem_tune.cu", "sem_cg.cu", "sem_pcg.cu", "sem_mixed.cu", "sem_batch.cu", "sem_serve.cu", "sem_probe.cu", "sem_dist.cu",
            "sem_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

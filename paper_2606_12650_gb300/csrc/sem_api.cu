@@ -43,6 +43,7 @@ struct Context {
     std::map<int64_t, Problem *> problems;
     std::map<int64_t, Batch *> batches;
     std::map<int64_t, Server *> servers;
+    std::map<int64_t, DistProblem *> dists;
     int64_t next_handle = 1;
     int32_t *status_dev = nullptr;
     int32_t *status_pinned = nullptr;
@@ -807,6 +808,120 @@ int run_cg_ax(ArgReader &R) {
     return rc != SEM_OK ? rc : launch_ax_cg(P);
 }
 
+// ---- one problem split across ranks (sem_dist.cu)
+DistProblem *get_dist(ArgReader &R, int k) {
+    const int64_t h = R.i(k, "handle");
+    if (R.err) return nullptr;
+    auto it = g.dists.find(h);
+    if (it == g.dists.end()) {
+        R.fail(SEM_EHANDLE, "unknown split-problem handle " + std::to_string(h));
+        return nullptr;
+    }
+    return it->second;
+}
+
+const sem_comm *get_comm(ArgReader &R, int k) {
+    return static_cast<const sem_comm *>(R.host(k, sizeof(sem_comm), "comm"));
+}
+
+int run_dist_mesh(ArgReader &R) {
+    if (!R.need(7)) return R.err;
+    const int64_t nx = R.i(0, "nx"), ny = R.i(1, "ny"), nz = R.i(2, "nz"), N = R.i(3, "N");
+    if (R.err) return R.err;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20))
+        return R.fail(SEM_EARG, "nx, ny, nz must be in [1, 2^20]");
+    const size_t nv = size_t(nx + 1) * size_t(ny + 1) * size_t(nz + 1);
+    const double *verts = static_cast<const double *>(R.arr(4, nv * 3 * sizeof(double), "verts"));
+    const int64_t nb = R.i(5, "neighbours");
+    int64_t *out = static_cast<int64_t *>(R.out(6, SEM_ARG_OUT_INT, "handle"));
+    if (R.err) return R.err;
+    if (nb < 0 || nb > 3) return R.fail(SEM_EARG, "neighbours must be in [0, 3]");
+    DistProblem *D = nullptr;
+    const int rc = dist_create(int(nx), int(ny), int(nz), int(N), verts, (nb & 1) != 0, (nb & 2) != 0, &D);
+    if (rc != SEM_OK) return rc;
+    const int64_t h = g.next_handle++;
+    g.dists[h] = D;
+    *out = h;
+    return SEM_OK;
+}
+
+int run_dist_info(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    DistProblem *D = get_dist(R, 0);
+    int64_t *o = static_cast<int64_t *>(R.out(1, SEM_ARG_OUT_INT, "nL"));
+    if (R.err) return R.err;
+    *o = dist_problem(D)->nL;
+    return SEM_OK;
+}
+
+int run_dist_ax(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    DistProblem *D = get_dist(R, 0);
+    if (R.err) return R.err;
+    Problem *P = dist_problem(D);
+    const size_t vb = size_t(P->nL) * sizeof(double);
+    const double *x = static_cast<const double *>(R.arr(1, vb, "x"));
+    double *y = static_cast<double *>(R.arr(2, vb, "y"));
+    if (R.err) return R.err;
+    if (x == y) return R.fail(SEM_EARG, "x and y must not alias");
+    return launch_ax(P, x, y);
+}
+
+int run_dist_gs(ArgReader &R) {
+    if (!R.need(3)) return R.err;
+    DistProblem *D = get_dist(R, 0);
+    if (R.err) return R.err;
+    double *u = static_cast<double *>(R.arr(1, size_t(dist_problem(D)->nL) * sizeof(double), "u"));
+    const sem_comm *comm = get_comm(R, 2);
+    if (R.err) return R.err;
+    const int rc = dist_gs(D, u, comm);
+    return rc != SEM_OK ? rc : sync_stream("dist_gs");
+}
+
+int run_dist_dot(ArgReader &R) {
+    if (!R.need(5)) return R.err;
+    DistProblem *D = get_dist(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(dist_problem(D)->nL) * sizeof(double);
+    const double *u = static_cast<const double *>(R.arr(1, vb, "u"));
+    const double *v = static_cast<const double *>(R.arr(2, vb, "v"));
+    const sem_comm *comm = get_comm(R, 3);
+    double *o = static_cast<double *>(R.out(4, SEM_ARG_OUT_DOUBLE, "result"));
+    if (R.err) return R.err;
+    return dist_dot(D, u, v, comm, o);
+}
+
+int run_dist_cg_solve(ArgReader &R) {
+    if (!R.need(9)) return R.err;
+    DistProblem *D = get_dist(R, 0);
+    if (R.err) return R.err;
+    const size_t vb = size_t(dist_problem(D)->nL) * sizeof(double);
+    const double *b = static_cast<const double *>(R.arr(1, vb, "b"));
+    double *x = static_cast<double *>(R.arr(2, vb, "x"));
+    const double tol = R.d(3, "tol");
+    const int64_t maxit = R.i(4, "maxit");
+    const sem_comm *comm = get_comm(R, 5);
+    if (R.err) return R.err;
+    if (maxit < 0 || maxit > (1 << 30)) return R.fail(SEM_EARG, "maxit must be in [0, 2^30]");
+    double *hist = static_cast<double *>(R.host(6, size_t(maxit + 1) * sizeof(double), "hist", true));
+    int64_t *oit = static_cast<int64_t *>(R.out(7, SEM_ARG_OUT_INT, "iters"));
+    double *ores = static_cast<double *>(R.out(8, SEM_ARG_OUT_DOUBLE, "rel_res"));
+    if (R.err) return R.err;
+    if (b == x) return R.fail(SEM_EARG, "b and x must not alias");
+    return dist_cg_solve(D, b, x, tol, int(maxit), hist, comm, oit, ores);
+}
+
+int run_dist_free(ArgReader &R) {
+    if (!R.need(1)) return R.err;
+    const int64_t h = R.i(0, "handle");
+    if (R.err) return R.err;
+    auto it = g.dists.find(h);
+    if (it == g.dists.end()) return R.fail(SEM_EHANDLE, "unknown split-problem handle");
+    dist_destroy(it->second);
+    g.dists.erase(it);
+    return SEM_OK;
+}
+
 int run_peak_fma(ArgReader &R) {
     if (!R.need(3)) return R.err;
     const int64_t dtype = R.i(0, "dtype"), iters = R.i(1, "iters");
@@ -1027,6 +1142,13 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "serve_drain") rc = run_serve_drain(R);
     else if (k == "serve_close") rc = run_serve_close(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
+    else if (k == "dist_mesh") rc = run_dist_mesh(R);
+    else if (k == "dist_info") rc = run_dist_info(R);
+    else if (k == "dist_ax") rc = run_dist_ax(R);
+    else if (k == "dist_gs") rc = run_dist_gs(R);
+    else if (k == "dist_dot") rc = run_dist_dot(R);
+    else if (k == "dist_cg_solve") rc = run_dist_cg_solve(R);
+    else if (k == "dist_free") rc = run_dist_free(R);
     else if (k == "autotune") rc = run_autotune(R);
     else if (k == "autotune_get") rc = run_autotune_get(R);
     else if (k == "autotune_set") rc = run_autotune_set(R);
@@ -1052,6 +1174,8 @@ int sem_finalize(void) {
     g.batches.clear();
     for (auto &kv : g.problems) problem_destroy(kv.second);
     g.problems.clear();
+    for (auto &kv : g.dists) dist_destroy(kv.second);
+    g.dists.clear();
     for (auto &kv : g.mirrors) dev_free(kv.second.dev);
     g.mirrors.clear();
     dev_free(g.status_dev);

@@ -240,6 +240,16 @@ int64_t serve_nodes_of(const Server *S, int64_t ticket);
 double serve_now(const Server *S);
 void serve_close(Server *S);
 
+// ---- one problem split by element slabs across ranks (sem_dist.cu) ---------
+struct DistProblem;
+int dist_create(int nx, int ny, int nz, int N, const double *verts_dev, bool below, bool above, DistProblem **out);
+void dist_destroy(DistProblem *D);
+Problem *dist_problem(DistProblem *D);
+int dist_gs(DistProblem *D, double *u, const sem_comm *comm);
+int dist_dot(DistProblem *D, const double *u, const double *v, const sem_comm *comm, double *out);
+int dist_cg_solve(DistProblem *D, const double *b, double *x, double tol, int maxit, double *hist,
+                  const sem_comm *comm, int64_t *iters, double *rel_res);
+
 // ---- device facts (sem_probe.cu) --------------------------------------------
 int probe_fma_rate(int dtype, int iters, double *flops_per_s);   // dtype 0: f64, 1: f32
 

@@ -143,6 +143,11 @@ class DevicePtr(int):
     """A raw device address (SEM_ARG_DEVICE)."""
 
 
+class HostPtr(int):
+    """The address of a host object (a ctypes structure) passed for the
+    duration of the call (SEM_ARG_HOST)."""
+
+
 class HostArray:
     """A small host numpy array passed by address for the duration of the
     call (SEM_ARG_HOST): read and/or written by libsem."""
@@ -171,6 +176,9 @@ def _marshal(a) -> SemArg:
     elif isinstance(a, HostArray):
         arg.kind = ARG_HOST
         arg.v.ptr = a.arr.__array_interface__["data"][0]
+    elif isinstance(a, HostPtr):
+        arg.kind = ARG_HOST
+        arg.v.ptr = int(a)
     elif isinstance(a, DevicePtr):
         arg.kind = ARG_DEVICE
         arg.v.ptr = int(a)
