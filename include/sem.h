@@ -192,6 +192,16 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *                                       vectors (p = r + beta p, w = A_local p,
  *                                       <p, w>), with the stop flag cleared; for
  *                                       timing after a cg_solve (changes p)
+ *   "wait_probe" limit_ns (1e3 .. 1e8), OUT copied
+ *               Self-test of failure detection: a one-block kernel copies 64
+ *               bytes with the TMA engine (waited for on its own mbarrier),
+ *               then runs the operator kernels' bounded mbarrier wait on a
+ *               barrier whose byte count is never supplied; the wait gives up
+ *               after ~limit_ns and sets the device status word.  copied
+ *               receives the last copied value (7.5) when the copy landed and
+ *               the wait ran out (-1 otherwise).  The next sem_sync or solve
+ *               returns SEM_ETIMEDOUT (the message names the wait) and clears
+ *               the word; nothing is left in flight and later calls work.
  *   "peak_fma"  dtype (0 f64, 1 f32), iters, OUT flops_per_s
  *               measured FMA issue rate of the FP64 or FP32 pipe (device fact
  *               for the ALU roofline; not part of the method)

@@ -167,8 +167,11 @@ int poll_status() {
         *g.status_pinned = 0;
         cudaMemsetAsync(g.status_dev, 0, sizeof(int32_t), g.cur_stream);
         cudaStreamSynchronize(g.cur_stream);
-        char buf[128];
-        snprintf(buf, sizeof buf, "a bounded device wait gave up (status %d)", code);
+        char buf[192];
+        snprintf(buf, sizeof buf,
+                 "a bounded device wait gave up (status %d: %s)", code,
+                 code == kStatusMbarTimeout ? "an mbarrier wait for a TMA copy into shared memory ran past its limit"
+                                            : "unknown wait");
         return set_error(SEM_ETIMEDOUT, buf);
     }
     return SEM_OK;
@@ -922,6 +925,15 @@ int run_dist_free(ArgReader &R) {
     return SEM_OK;
 }
 
+int run_wait_probe(ArgReader &R) {
+    if (!R.need(2)) return R.err;
+    const int64_t limit = R.i(0, "limit_ns");
+    double *out = static_cast<double *>(R.out(1, SEM_ARG_OUT_DOUBLE, "copied"));
+    if (R.err) return R.err;
+    if (limit < 0) return R.fail(SEM_EARG, "limit_ns must be positive");
+    return probe_wait_timeout(uint64_t(limit), out);
+}
+
 int run_peak_fma(ArgReader &R) {
     if (!R.need(3)) return R.err;
     const int64_t dtype = R.i(0, "dtype"), iters = R.i(1, "iters");
@@ -1142,6 +1154,7 @@ int sem_run(const char *kernel, int nargs, const sem_arg *args) {
     else if (k == "serve_drain") rc = run_serve_drain(R);
     else if (k == "serve_close") rc = run_serve_close(R);
     else if (k == "peak_fma") rc = run_peak_fma(R);
+    else if (k == "wait_probe") rc = run_wait_probe(R);
     else if (k == "dist_mesh") rc = run_dist_mesh(R);
     else if (k == "dist_info") rc = run_dist_info(R);
     else if (k == "dist_ax") rc = run_dist_ax(R);

@@ -252,5 +252,7 @@ int dist_cg_solve(DistProblem *D, const double *b, double *x, double tol, int ma
 
 // ---- device facts (sem_probe.cu) --------------------------------------------
 int probe_fma_rate(int dtype, int iters, double *flops_per_s);   // dtype 0: f64, 1: f32
+// failure-detection self-test: a bounded mbarrier wait that runs out (status word set)
+int probe_wait_timeout(uint64_t limit_ns, double *copied_value);
 
 }  // namespace sem
