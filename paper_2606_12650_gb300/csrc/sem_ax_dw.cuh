@@ -223,6 +223,13 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
     const int a = ab % NQ, b = ab / NQ;
     const bool act = eb < ne;
     const int64_t nb = (e0 + eb) * NP;
+    // CG: the x values of the thread's t line (deferred update) are loaded
+    // before the slab wait, so their latency overlaps the copy
+    double xpre[CG ? NQ : 1];
+    if (CG && act && xs) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) xpre[k] = xs[nb + k * NQ2 + b * NQ + a];
+    }
     const bool ok = mbar_wait_bounded(bar, phase, status);
     if (__syncthreads_or(!ok)) {
         mbar_wait_bounded(bar, phase, nullptr);  // let copies in flight land before leaving
@@ -249,7 +256,7 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
             double v;
             if (CG) {
                 const double zq = PRE ? dinv[nb + k * NQ2 + tq] * s1[q] : s1[q];
-                if (xs) xs[nb + k * NQ2 + tq] = fma(xalpha, s2[q], xs[nb + k * NQ2 + tq]);
+                if (xs) xs[nb + k * NQ2 + tq] = fma(xalpha, s2[q], xpre[k]);
                 v = fma(beta, s2[q], zq);
                 p[nb + k * NQ2 + tq] = v;
             } else {
