@@ -38,27 +38,6 @@ void dw_release(Problem *P) {
     P->Gdw = nullptr;
 }
 
-static dwf dw_host(double d) {
-    const float h = float(d);
-    return {h, float(d - double(h))};
-}
-
-// Even-odd halves of M (row-major nq x nq), formed in FP64, then split.
-static EoMatDW eo_coefficients_dw(const double *M, int nq) {
-    EoMatDW c{};
-    const int N = nq - 1, H = nq / 2;
-    for (int i = 0; i < H; ++i)
-        for (int l = 0; l < H; ++l) {
-            c.e[i * H + l] = dw_host(0.5 * (M[i * nq + l] + M[i * nq + N - l]));
-            c.o[i * H + l] = dw_host(0.5 * (M[i * nq + l] - M[i * nq + N - l]));
-        }
-    if (nq & 1) {
-        for (int l = 0; l < H; ++l) c.o[H * H + l] = dw_host(0.5 * (M[H * nq + l] - M[H * nq + N - l]));
-        for (int i = 0; i < H; ++i) c.m[i] = dw_host(M[i * nq + H]);
-    }
-    return c;
-}
-
 template <int NQ, bool CG, bool PRE>
 static int launch_dw_nq(const Problem *Pb, const AxDwArgs &L) {
     const int nt = line_threads(NQ, L.epb);
@@ -76,7 +55,7 @@ static int launch_dw_nq(const Problem *Pb, const AxDwArgs &L) {
         sm_set = sm;
     }
     const int64_t blocks = (Pb->E + L.epb - 1) / L.epb;
-    if (CG && blocks > kMaxPartials) return set_error(SEM_ERANGE, "ax dw: too many elements for one launch");
+    if (CG && blocks > Pb->partials_cap) return set_error(SEM_ERANGE, "ax dw: more blocks than reduction slots");
     kern<<<unsigned(blocks), nt, sm, stream()>>>(L);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "ax_dw_kernel");

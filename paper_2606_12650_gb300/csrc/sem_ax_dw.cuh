@@ -158,6 +158,28 @@ __device__ __forceinline__ void eo_apply_dw(const dwf (&u)[NQ], dwf (&y)[NQ], co
     }
 }
 
+// Host: even-odd halves of M (row-major nq x nq), formed in FP64, then split
+// into double-word pairs (h = rn(d), l = rn(d - h)).
+inline dwf dw_split_host(double d) {
+    const float h = float(d);
+    return {h, float(d - double(h))};
+}
+
+inline EoMatDW eo_coefficients_dw(const double *M, int nq) {
+    EoMatDW c{};
+    const int N = nq - 1, H = nq / 2;
+    for (int i = 0; i < H; ++i)
+        for (int l = 0; l < H; ++l) {
+            c.e[i * H + l] = dw_split_host(0.5 * (M[i * nq + l] + M[i * nq + N - l]));
+            c.o[i * H + l] = dw_split_host(0.5 * (M[i * nq + l] - M[i * nq + N - l]));
+        }
+    if (nq & 1) {
+        for (int l = 0; l < H; ++l) c.o[H * H + l] = dw_split_host(0.5 * (M[H * nq + l] - M[H * nq + N - l]));
+        for (int i = 0; i < H; ++i) c.m[i] = dw_split_host(M[i * nq + H]);
+    }
+    return c;
+}
+
 struct AxDwArgs {
     AxArgs<double, double> a;   // FP64 vectors, state, partials (a.G unused)
     const float *Gdw;           // [nL][6][2]: (h, l) of each FP64 factor

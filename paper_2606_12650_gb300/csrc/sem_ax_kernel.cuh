@@ -296,7 +296,7 @@ static int launch_ax_nq(const Problem *Pb, const AxArgs<T, GT> &a) {
     const int arc = ax_attr<NQ, T, GT, CG, PRE>();
     if (arc != SEM_OK) return arc;
     const int64_t blocks = (Pb->E + EPB - 1) / EPB;
-    if (CG && blocks > kMaxPartials) return set_error(SEM_ERANGE, "ax: too many elements for one launch");
+    if (CG && blocks > Pb->partials_cap) return set_error(SEM_ERANGE, "ax: more blocks than reduction slots");
     ax_kernel<NQ, EPB, T, GT, CG, PRE><<<unsigned(blocks), S::NT, S::SMEM, stream()>>>(a);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "ax_kernel");

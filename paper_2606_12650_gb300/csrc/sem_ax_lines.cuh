@@ -466,7 +466,7 @@ static int launch_lines_nq(const Problem *Pb, const AxLineArgs<T, GT> &L) {
         sm_set = sm;
     }
     const int64_t blocks = (Pb->E + L.epb - 1) / L.epb;
-    if (CG && blocks > kMaxPartials) return set_error(SEM_ERANGE, "ax lines: too many elements for one launch");
+    if (CG && blocks > Pb->partials_cap) return set_error(SEM_ERANGE, "ax lines: more blocks than reduction slots");
     kern<<<unsigned(blocks), nt, sm, stream()>>>(L);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "ax_lines_kernel");

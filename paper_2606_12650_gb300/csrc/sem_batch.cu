@@ -8,9 +8,9 @@
 // counter (dynamic load balance across problems of very different cost); a
 // device-side switch on N dispatches to the body compiled for that order.
 // The operator body and the elements per pass follow the per-order tuner's
-// table for the batch's precision: the line body (sem_ax_lines.cuh) with the
-// tuned elements per block, capped at what 256 threads hold, or the column
-// body with 256 / (N+1)^2 elements.  Items of problems whose solve finished
+// table for the batch's precision: the line body (sem_ax_lines.cuh), in
+// double-word arithmetic for FP64 batches where the table chose that variant
+// (sem_ax_dw.cuh), or the column body, passes of 256 / (N+1)^2 elements.  Items of problems whose solve finished
 // are dropped from the lists between rounds (their order within a problem,
 // and so its reductions, never change).
 //
@@ -38,7 +38,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "sem_ax_lines.cuh"
+#include "sem_ax_dw.cuh"
 #include "sem_box.cuh"
 #include "sem_device.cuh"
 #include "sem_internal.h"
@@ -54,6 +54,7 @@ struct BatchProb {
     BoxDims bd;                     // the box with its fast divisors
     int64_t E, nL;
     const double *G;
+    const float *Gdw;               // double-word factors (FP64 batches with the double-word body)
     const __nv_bfloat16 *G16;
     const float *G32;
     double *x, *r, *p, *w;          // FP64 CG vectors / refinement x, r
@@ -77,6 +78,7 @@ struct BatchItem {
     int64_t first;  // first element (operator) or first local node (vector)
     int count;      // elements or nodes
     int group;      // operator items: elements per pass of the line body; 0 = column body
+    int dw;         // operator items of FP64 batches: the line body in double-word arithmetic
 };
 
 struct BatchQueue {
@@ -143,6 +145,7 @@ __constant__ float c_D32[kMaxQ - 1][kMaxQ * kMaxQ];
 // even-odd coefficients of D ([0]) and D^T ([1]) for the line body
 __constant__ EoMat<double> c_E64[kMaxQ - 1][2];
 __constant__ EoMat<float> c_E32[kMaxQ - 1][2];
+__constant__ EoMatDW c_EDW[kMaxQ - 1][2];
 
 template <typename T>
 __device__ __forceinline__ const EoMat<T> &const_eo(int nq, int which);
@@ -262,6 +265,27 @@ __device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, cons
     return true;
 }
 
+// The double-word line body (FP64 batches): same passes as batch_lines_item.
+template <int NQ, bool CG>
+__device__ __noinline__ bool batch_dw_item(const double *xin, double *yout, double *pv, const float *Gdw, double beta,
+                                           int64_t first, int count, int group, double *regA, uint64_t *bar,
+                                           uint32_t *phase, int32_t *status, double *pt) {
+    double acc = 0.0;
+    for (int g = 0; g < count; g += group) {
+        double part = 0.0;
+        const bool ok = lines_group_dw<NQ, CG, false>(xin, yout, pv, Gdw, c_EDW[NQ - 2][0], c_EDW[NQ - 2][1], beta,
+                                                      0.0, nullptr, nullptr, first + g, min(group, count - g), group,
+                                                      regA, bar, *phase, status, &part);
+        *phase ^= 1u;
+        if (!ok) return false;
+        acc += part;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    *pt = acc;
+    return true;
+}
+
 // mode: 0 = FP64 CG (p = r + beta p, w = A p), 1 = FP64 plain (w = A x),
 //       2 = FP32 inner CG on the FP32 vectors
 // FP32 items are HBM-bound: 4 CTAs per SM (<= 64 registers) for latency
@@ -301,6 +325,13 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2) batch_a
         switch (item.nq) {
 #define SEM_BAX(Q)                                                                                       \
     case Q:                                                                                              \
+        if constexpr (std::is_same<T, double>::value) {                                                  \
+            if (item.dw) {                                                                               \
+                ok = batch_dw_item<Q, CG>(xin, yout, pv, P.Gdw, beta, item.first, item.count, item.group,  \
+                                          regA, bar, &phase, status, &pt);                               \
+                break;                                                                                   \
+            }                                                                                            \
+        }                                                                                                \
         ok = item.group ? batch_lines_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,   \
                                                          item.group, regA, bar, &phase, status, &pt)       \
                         : batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,      \
@@ -586,6 +617,7 @@ static int batch_attrs(Batch *B) {
         }
         static EoMat<double> e64[kMaxQ - 1][2];
         static EoMat<float> e32[kMaxQ - 1][2];
+        static EoMatDW edw[kMaxQ - 1][2];
         for (int N = 1; N <= kMaxQ - 1; ++N) {
             const int nq = N + 1;
             double Dt[kMaxQ * kMaxQ];
@@ -595,11 +627,14 @@ static int batch_attrs(Batch *B) {
             e64[N - 1][1] = eo_coefficients<double>(Dt, nq);
             e32[N - 1][0] = eo_coefficients<float>(h64[N - 1], nq);
             e32[N - 1][1] = eo_coefficients<float>(Dt, nq);
+            edw[N - 1][0] = eo_coefficients_dw(h64[N - 1], nq);
+            edw[N - 1][1] = eo_coefficients_dw(Dt, nq);
         }
         int rc = cuda_check(cudaMemcpyToSymbol(c_D64, h64, sizeof h64), "batch: D table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_D32, h32, sizeof h32), "batch: D table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E64, e64, sizeof e64), "batch: even-odd table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E32, e32, sizeof e32), "batch: even-odd table");
+        if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_EDW, edw, sizeof edw), "batch: even-odd table");
         const int a = int(batch_ax_smem<double>()), f = int(batch_ax_smem<float>());
         if (rc == SEM_OK)
             rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 0>,
@@ -780,7 +815,15 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         // item holds several passes (~kAxItemNodes local nodes)
         const int full = kBatchThreads / (P->nq * P->nq);
         const TuneChoice c = tune_get(B->mode == 0 ? kTuneF64 : (B->mode == 1 ? kTuneF32G16 : kTuneF32G32), P->nq);
-        // (the double-word FP64 variant runs the FP64 line body here)
+        // the double-word variant: its line body in FP64 batches (factors
+        // made here, before any capture); mixed batches (whose FP64 operator
+        // runs only for the refinement residual) keep the FP64 line body
+        const bool dw = B->mode == 0 && c.variant == kAxLinesDW;
+        if (dw) {
+            rc = dw_prepare(P);
+            if (rc != SEM_OK) break;
+            q.Gdw = P->Gdw;
+        }
         const bool lines = c.variant == kAxLines || c.variant == kAxLinesPrefetch || c.variant == kAxLinesStaged ||
                            c.variant == kAxLinesDW;
         const int group = full;
@@ -788,7 +831,8 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         const int per_item = group * std::max(1, kAxItemNodes / (np * group));
         q.ax_first = int(ax.size());
         for (int64_t e = 0; e < P->E; e += per_item)
-            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(per_item, P->E - e)), lines ? group : 0});
+            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(per_item, P->E - e)), lines ? group : 0,
+                                   dw ? 1 : 0});
         q.ax_count = int(ax.size()) - q.ax_first;
         const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
         q.vec_first = int(vec.size());

@@ -214,7 +214,8 @@ __device__ __forceinline__ double finish_partials(const double *partials, int n,
 // the end of the launch (on GB300 FP64 runs at 1/64 of the FP32 rate).
 __device__ __forceinline__ bool publish_grouped(double v0, double *partials, uint32_t *ticket) {
     __shared__ int s_last;
-    uint32_t *gt = group_tickets(partials);
+    const int64_t cap = partials_capacity(partials);
+    uint32_t *gt = group_tickets(partials, cap);
     const int b = int(blockIdx.x), g = b / kSumGroup, g0 = g * kSumGroup;
     const int gn = min(kSumGroup, int(gridDim.x) - g0);
     if (threadIdx.x == 0) {
@@ -231,7 +232,7 @@ __device__ __forceinline__ bool publish_grouped(double v0, double *partials, uin
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (threadIdx.x == 0) {
-            partials[kMaxPartials + g] = s;
+            partials[cap + g] = s;
             gt[g] = 0u;
             __threadfence();
             const uint32_t ng = (gridDim.x + kSumGroup - 1) / kSumGroup;
@@ -245,8 +246,10 @@ __device__ __forceinline__ bool publish_grouped(double v0, double *partials, uin
 // Zero the group tickets (grid-stride): at the start of every solve, so that
 // a launch that gave up half-way (a timed-out copy) leaves no stale count.
 __device__ __forceinline__ void reset_group_tickets(double *partials) {
-    uint32_t *gt = group_tickets(partials);
-    for (int i = int(blockIdx.x * blockDim.x + threadIdx.x); i < kMaxSumGroups; i += int(gridDim.x * blockDim.x))
+    const int64_t cap = partials_capacity(partials);
+    uint32_t *gt = group_tickets(partials, cap);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < cap / kSumGroup;
+         i += int64_t(gridDim.x) * blockDim.x)
         gt[i] = 0u;
 }
 
@@ -257,7 +260,8 @@ __device__ __forceinline__ double finish_grouped(const double *partials, uint32_
     if (threadIdx.x < 32) {
         __threadfence();
         const int ng = int((gridDim.x + kSumGroup - 1) / kSumGroup);
-        for (int q = threadIdx.x; q < ng; q += 32) s += __ldcg(partials + kMaxPartials + q);
+        const int64_t cap = partials_capacity(partials);
+        for (int q = threadIdx.x; q < ng; q += 32) s += __ldcg(partials + cap + q);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (threadIdx.x == 0) *ticket = 0u;

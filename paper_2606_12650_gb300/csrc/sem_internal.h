@@ -15,17 +15,29 @@
 namespace sem {
 
 constexpr int kMaxQ = 10;          // N <= 9  ->  N+1 <= 10 points per direction
-constexpr int kMaxPartials = 1 << 17;
 // Grid sums of many blocks in two levels (publish_grouped): groups of
-// kSumGroup consecutive blocks.  A problem's partials buffer holds
-// kMaxPartials block partials, then kMaxSumGroups group sums (doubles), then
-// kMaxSumGroups group tickets (uint32, zero between launches).
+// kSumGroup consecutive blocks.  A problem's partials buffer holds `cap`
+// block partials, then cap / kSumGroup group sums (doubles), then
+// cap / kSumGroup group tickets (uint32, zero between launches); cap is at
+// least kMinPartials and at least the problem's element count (the largest
+// grid any of its launches uses: the operator at one element per block), a
+// multiple of kSumGroup, and is stored as a uint64 in the 16 bytes before
+// the buffer, where device code reads it.
 constexpr int kSumGroup = 32;
-constexpr int kMaxSumGroups = kMaxPartials / kSumGroup;
-constexpr size_t kPartialsBytes =
-    sizeof(double) * (kMaxPartials + kMaxSumGroups) + sizeof(uint32_t) * kMaxSumGroups;
-__host__ __device__ inline uint32_t *group_tickets(double *partials) {
-    return reinterpret_cast<uint32_t *>(partials + kMaxPartials + kMaxSumGroups);
+constexpr int64_t kMinPartials = 1 << 17;
+inline int64_t partials_cap(int64_t E) {
+    const int64_t e = (E + kSumGroup - 1) / kSumGroup * kSumGroup;
+    return e > kMinPartials ? e : kMinPartials;
+}
+// bytes of the allocation (header included)
+inline size_t partials_bytes(int64_t cap) {
+    return 16 + sizeof(double) * size_t(cap + cap / kSumGroup) + sizeof(uint32_t) * size_t(cap / kSumGroup);
+}
+__device__ __forceinline__ int64_t partials_capacity(const double *partials) {
+    return int64_t(__ldg(reinterpret_cast<const unsigned long long *>(partials) - 2));
+}
+__host__ __device__ inline uint32_t *group_tickets(double *partials, int64_t cap) {
+    return reinterpret_cast<uint32_t *>(partials + cap + cap / kSumGroup);
 }
 
 // Small per-problem constants passed to kernels by value (constant bank).
@@ -87,7 +99,8 @@ struct Problem {
     double *x = nullptr, *r = nullptr, *p = nullptr, *w = nullptr;
     double *dinv = nullptr;        // Jacobi: 1 / diag(A) (0 on masked nodes), on first PCG use
     cudaGraphExec_t graph_pcg = nullptr;
-    double *partials = nullptr;
+    double *partials = nullptr;    // after a 16-byte header holding partials_cap (see above)
+    int64_t partials_cap = 0;
     CgState *st = nullptr;
     CgState *st_host = nullptr;    // pinned mirror for polling
     cudaGraphExec_t graph = nullptr;

@@ -71,20 +71,21 @@ double serve_now(const Server *S) {
 
 // Device bytes a request holds from admission until its result is fetched,
 // from the node count: FP64 geometry (48), mass (8), CG vectors (32),
-// right-hand side (8) and the retired result (8) per node, plus for mixed
-// precision BF16/FP32 factors (12 or 24) and FP32 inner vectors (16); and per
-// problem its reduction partials, two CG states and the vertex copy, plus
-// 64 KB of allocation granularity.
-static size_t request_bytes(int mode, int64_t nL, int64_t n_verts) {
+// right-hand side (8) and the retired result (8) per node, plus for FP64 the
+// double-word copy of the factors (48; counted whichever operator body the
+// tuner picked), for mixed precision BF16/FP32 factors (12 or 24) and FP32
+// inner vectors (16); and per problem its reduction partials, two CG states
+// and the vertex copy, plus 64 KB of allocation granularity.
+static size_t request_bytes(int mode, int nx, int ny, int nz, int64_t nL) {
     size_t per = 48 + 8 + 32 + 8 + 8;
+    if (mode == 0) per += 48;   // the double-word copy of G (FP64 batches' double-word body)
     if (mode == 1) per += 12 + 16;
     if (mode == 2) per += 24 + 16;
-    return size_t(nL) * per + kPartialsBytes + 2 * sizeof(CgState) + size_t(n_verts) * 3 * sizeof(double) +
-           (size_t(1) << 16);
+    const int64_t n_verts = int64_t(nx + 1) * (ny + 1) * (nz + 1);
+    return size_t(nL) * per + partials_bytes(partials_cap(int64_t(nx) * ny * nz)) + 2 * sizeof(CgState) +
+           size_t(n_verts) * 3 * sizeof(double) + (size_t(1) << 16);
 }
-static size_t request_bytes(int mode, const ServeReq *q) {
-    return request_bytes(mode, q->nL, int64_t(q->nx + 1) * (q->ny + 1) * (q->nz + 1));
-}
+static size_t request_bytes(int mode, const ServeReq *q) { return request_bytes(mode, q->nx, q->ny, q->nz, q->nL); }
 
 int serve_open(int capacity, double budget_gb, int mode, double tol, double inner_tol, int K, int maxit,
                Server **out) {
@@ -110,7 +111,7 @@ int serve_submit(Server *S, int nx, int ny, int nz, int N, const double *verts, 
     if (N < 1 || N > kMaxQ - 1) return set_error(SEM_EARG, "serve_submit: N must be in [1, 9]");
     const int64_t nL = int64_t(nx) * ny * nz * (N + 1) * (N + 1) * (N + 1);
     if (nL >= (int64_t(1) << 31) - 1) return set_error(SEM_ERANGE, "serve_submit: problem too large");
-    if (request_bytes(S->mode, nL, int64_t(nx + 1) * (ny + 1) * (nz + 1)) > S->budget)
+    if (request_bytes(S->mode, nx, ny, nz, nL) > S->budget)
         return set_error(SEM_ENOMEM, "serve_submit: the request alone exceeds the server's HBM budget");
     ServeReq *q = new ServeReq();
     q->ticket = S->next_ticket++;

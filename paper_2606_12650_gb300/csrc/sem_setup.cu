@@ -383,7 +383,9 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         P->r = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->p = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->w = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
-        P->partials = static_cast<double *>(dev_alloc(kPartialsBytes));
+        P->partials_cap = partials_cap(P->E);
+        unsigned char *pb = static_cast<unsigned char *>(dev_alloc(partials_bytes(P->partials_cap)));
+        P->partials = pb ? reinterpret_cast<double *>(pb + 16) : nullptr;
         P->st = static_cast<CgState *>(dev_alloc(sizeof(CgState)));
         if (!P->x || !P->r || !P->p || !P->w || !P->partials || !P->st) rc = SEM_ENOMEM;
     }
@@ -394,8 +396,15 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
     }
     if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(P->st, 0, sizeof(CgState), stream()), "mesh: state");
     if (rc == SEM_OK)
-        rc = cuda_check(cudaMemsetAsync(group_tickets(P->partials), 0, sizeof(uint32_t) * kMaxSumGroups, stream()),
+        rc = cuda_check(cudaMemsetAsync(group_tickets(P->partials, P->partials_cap), 0,
+                                        sizeof(uint32_t) * size_t(P->partials_cap / kSumGroup), stream()),
                         "mesh: group tickets");
+    if (rc == SEM_OK) {
+        static_assert(sizeof(int64_t) == 8, "capacity header");
+        rc = cuda_check(cudaMemcpyAsync(reinterpret_cast<unsigned char *>(P->partials) - 16, &P->partials_cap,
+                                        sizeof(int64_t), cudaMemcpyHostToDevice, stream()),
+                        "mesh: partials header");
+    }
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
     if (rc != SEM_OK) {
         problem_destroy(P);
@@ -444,7 +453,8 @@ void problem_destroy(Problem *P) {
     if (P->dinv) dev_free(P->dinv);
     mixed_release(P);
     dw_release(P);
-    double *dptrs[] = {P->verts, P->G, P->B, P->c, P->x, P->r, P->p, P->w, P->partials};
+    if (P->partials) dev_free(reinterpret_cast<unsigned char *>(P->partials) - 16);
+    double *dptrs[] = {P->verts, P->G, P->B, P->c, P->x, P->r, P->p, P->w};
     for (double *q : dptrs)
         if (q) dev_free(q);
     int32_t *iptrs[] = {P->sh_ptr, P->sh_idx, P->msk_idx};

@@ -29,16 +29,18 @@ bool g_init = false;
 uint64_t g_epoch = 1;
 
 // Built-in table: the winners of tuning runs on GB300 with ~17 M local
-// nodes per problem (E = 128^3 at N = 1 down to 26^3 at N = 9; CG operator,
+// nodes per problem (E = 129^3 at N = 1 down to 26^3 at N = 9; CG operator,
 // 10 launches per candidate), as {variant, elements per block} indexed by
 // N + 1 (entries 0 and 1 unused); the run-time tuner replaces entries for
-// the problems at hand.
+// the problems at hand.  FP64: the double-word line kernel at every order
+// (e.g. N = 3: 281 us against 1203 us for the DFMA line kernel; N = 7: 371
+// against 1579; N = 9: 576 against 2117).
 struct DefaultEntry {
     int variant, epb;
 };
 constexpr DefaultEntry kDefault[kTuneKinds][kMaxQ + 1] = {
     // FP64
-    {{0, 0}, {0, 0}, {0, 0}, {1, 28}, {0, 0}, {1, 10}, {1, 7}, {1, 7}, {1, 3}, {1, 3}, {1, 2}},
+    {{0, 0}, {0, 0}, {5, 32}, {5, 14}, {5, 8}, {5, 5}, {5, 7}, {5, 5}, {5, 4}, {5, 3}, {5, 5}},
     // FP32, FP32 factors
     {{2, 0}, {2, 0}, {2, 0}, {2, 0}, {2, 0}, {1, 10}, {1, 10}, {1, 5}, {1, 3}, {1, 3}, {1, 2}},
     // FP32, BF16 factors
