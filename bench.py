@@ -59,7 +59,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 AX_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
               for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax.cu", "sem_ax_lines64.cu", "sem_device.cuh",
-                        "sem_internal.h", "sem_ax_dw.cuh", "sem_ax_dw.cu")]
+                        "sem_internal.h", "sem_ax_dw.cuh", "sem_ax_dw.cu", "sem_dw.cuh")]
 GOLDEN_SMALL = os.path.join(ROOT, "tests", "golden", "oracle_cg_E64_N7.npz")
 AX32_SOURCES = [os.path.join(ROOT, "paper_2606_12650_gb300", "csrc", f)
                 for f in ("sem_ax_kernel.cuh", "sem_ax_lines.cuh", "sem_ax32.cu", "sem_ax_lines32.cu", "sem_ax32p.cuh",

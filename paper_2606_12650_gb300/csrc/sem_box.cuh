@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 namespace sem {
 
@@ -80,8 +81,26 @@ __device__ __forceinline__ BoxNode box_node(int l, int nx, int ny, int nz) {
 }  // namespace sem
 
 #include "sem_device.cuh"
+#include "sem_dw.cuh"
 
 namespace sem {
+
+// Accumulators of <r, r>: FP64 or FP32 fma, or (FP64 CG update) double-word
+// FP32, which takes the reduction off GB300's 1/64-rate FP64 pipe; the
+// recurrences (copy sums, r -= alpha w) stay FP64.
+struct DwAcc {
+    dwf v;
+};
+__device__ __forceinline__ void acc_square(double &a, double r) { a = fma(r, r, a); }
+__device__ __forceinline__ void acc_square(float &a, float r) { a = fmaf(r, r, a); }
+__device__ __forceinline__ void acc_square(DwAcc &a, double r) { a.v = dw_add_square(a.v, r); }
+__device__ __forceinline__ double acc_value(double a) { return a; }
+__device__ __forceinline__ double acc_value(float a) { return double(a); }
+__device__ __forceinline__ double acc_value(const DwAcc &a) { return dw_to_double(a.v); }
+template <typename Acc>
+__device__ __forceinline__ Acc acc_zero() { return Acc(0); }
+template <>
+__device__ __forceinline__ DwAcc acc_zero<DwAcc>() { return DwAcc{{0.0f, 0.0f}}; }
 
 // Vector width for the update: V consecutive nodes of one row share the
 // element, j and k; V divides N+1 and V * sizeof(T) <= 16 bytes.
@@ -274,7 +293,7 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
         }
     }
     const bool owner_row = sy >= 0 && sz >= 0;
-    Acc rr = Acc(0);
+    Acc rr = acc_zero<Acc>();
 #pragma unroll
     for (int v = 0; v < V; ++v) {
         const bool masked = (v == 0 && mask_lo) || (v == V - 1 && mask_hi);
@@ -282,19 +301,19 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
             if (!DX) xv[v] = fma(alpha, pv[v], xv[v]);
             rv[v] = fma(-alpha, sv[v], rv[v]);
             if (owner_row && !((v == 0) && has_lo)) {
-                if (PRE) {
+                if constexpr (PRE) {
                     // <r, M^-1 r> for beta and <r, r> for the stop test
                     acc = fma(Acc(rv[v]), Acc(dv[v] * rv[v]), acc);
                     rr = fma(Acc(rv[v]), Acc(rv[v]), rr);
                 } else {
-                    acc = fma(Acc(rv[v]), Acc(rv[v]), acc);
+                    acc_square(acc, rv[v]);
                 }
             }
         }
     }
     if (!DX) vstore<T, V>(x + l0, xv);
     vstore<T, V>(r + l0, rv);
-    if (PRE) *acc_rr += rr;
+    if constexpr (PRE) *acc_rr += rr;
 }
 
 // Row-class mapping of update vectors to threads: a warp takes the same row
@@ -358,7 +377,7 @@ __global__ void __launch_bounds__(256, 5) cg_update_nodes_kernel(T *__restrict__
     __shared__ double scratch[256];
     if (st->done) return;
     const T alpha = T(st->alpha);
-    Acc acc = Acc(0);
+    Acc acc = acc_zero<Acc>();
     constexpr int V = UpdVec<NQ, T>::value;
     const int nv = nL / V;   // nL is a multiple of (N+1), hence of V
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nv; u += gridDim.x * blockDim.x)
@@ -366,10 +385,10 @@ __global__ void __launch_bounds__(256, 5) cg_update_nodes_kernel(T *__restrict__
     // all blocks of the resident wave reach this point together: block sums
     // in Acc when it is FP32, one warp's FP64 sum otherwise, grid sum in groups
     double bs;
-    if constexpr (sizeof(Acc) == 4)
+    if constexpr (std::is_same<Acc, float>::value)
         bs = double(block_sum_f32(acc, reinterpret_cast<float *>(scratch)));
     else
-        bs = block_sum_wide(double(acc), scratch);
+        bs = block_sum_wide(acc_value(acc), scratch);
     if (publish_grouped(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_grouped(partials, &st->ticket_up);
         if (threadIdx.x == 0) cg_close_iteration(st, rho_new);
@@ -391,14 +410,14 @@ __global__ void __launch_bounds__(256) cg_update_class_kernel(T *__restrict__ x,
     const int ntask = RM::tasks(E);
     const int lane = threadIdx.x & 31;
     const int nwarps = int(gridDim.x * blockDim.x) >> 5;
-    Acc acc = Acc(0);
+    Acc acc = acc_zero<Acc>();
     for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
         const int l0 = RM::l0(task, lane, E);
         if (l0 >= 0) update_vec<NQ, V, T, Acc, false, true>(x, r, p, w, l0, bd, alpha, acc);
     }
     // one warp's FP64 sum per block (13 instead of 40 warp-wide FP64 adds),
     // grid sum in groups
-    const double bs = block_sum_wide(double(acc), scratch);
+    const double bs = block_sum_wide(acc_value(acc), scratch);
     if (publish_grouped(bs, partials, &st->ticket_up)) {
         const double rho_new = finish_grouped(partials, &st->ticket_up);
         if (threadIdx.x == 0) cg_close_iteration(st, rho_new);

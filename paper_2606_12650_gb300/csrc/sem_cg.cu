@@ -181,7 +181,8 @@ int launch_x_finish(const Problem *P) {
 }
 
 int launch_cg_update(const Problem *P) {
-    return launch_update_rows<double, double>(P, P->x, P->r, P->p, P->w, P->st);
+    // <r, r> accumulated in double-word FP32 per thread (sem_box.cuh)
+    return launch_update_rows<double, DwAcc>(P, P->x, P->r, P->p, P->w, P->st);
 }
 
 // Iterations per captured graph: the host polls the stop flag once per replay.
