@@ -151,7 +151,13 @@ static void pinned_release_all() {
     g_pinned_free.clear();
 }
 
-cudaStream_t stream() { return g.cur_stream; }
+// Work a thread issues inside a StreamScope goes to that scope's stream (the
+// server admits requests on its own stream while a batch round runs on the
+// library stream).
+thread_local cudaStream_t g_stream_override = nullptr;
+cudaStream_t stream() { return g_stream_override ? g_stream_override : g.cur_stream; }
+StreamScope::StreamScope(cudaStream_t s) : prev(g_stream_override) { g_stream_override = s; }
+StreamScope::~StreamScope() { g_stream_override = prev; }
 int sm_count() { return g.prop.multiProcessorCount > 0 ? g.prop.multiProcessorCount : 1; }
 int32_t *status_word() { return g.status_dev; }
 int32_t *status_host() { return g.status_pinned; }

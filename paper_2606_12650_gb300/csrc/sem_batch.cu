@@ -119,6 +119,11 @@ struct Batch {
     int grid_ax64 = 0, grid_ax32 = 0;   // resident CTAs of the operator launches
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
+    // the buffers the captured round reads and its grids; the graph stays
+    // valid while the buffers stay in place and the grids stay the same
+    // (membership changes only rewrite the lists' contents and counts)
+    const void *graph_bufs[6] = {};
+    int graph_items[2] = {0, 0};    // power-of-two ceilings of the item counts at capture
 };
 
 template <int NQ>
@@ -562,10 +567,20 @@ static int batch_grid(const void *kern, size_t smem, int *out) {
     return SEM_OK;
 }
 
+// Grid of a persistent launch over n items: the resident CTAs, or fewer for
+// few items -- the next power of two of n, so that a captured round stays
+// valid while the item count changes within a factor of two (extra CTAs find
+// the queue empty and leave).
+static int items_grid(int resident, int n) {
+    int p = 1;
+    while (p < n && p < (1 << 30)) p <<= 1;
+    return std::max(1, std::min(resident, p));
+}
+
 template <typename T, typename GT, int MODE>
 static int launch_bax(Batch *B, int grid) {
     const size_t sm = batch_ax_smem<T>();
-    const int g = std::max(1, std::min(grid, B->n_ax));
+    const int g = items_grid(grid, B->n_ax);
     batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(B->d_probs, B->d_ax, B->part,
                                                                              B->tickets, B->ctl, status_word());
     count_launches(1);
@@ -591,7 +606,7 @@ static int launch_bvec(Batch *B) {
     int grid = 0;
     const int rcg = vec_grid<MODE>(&grid);
     if (rcg != SEM_OK) return rcg;
-    const int g = std::max(1, std::min(grid, B->n_vec));
+    const int g = items_grid(grid, B->n_vec);
     batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->part, B->tickets,
                                                                        B->ctl, B->finished_ids, A);
     count_launches(1);
@@ -842,14 +857,14 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     }
     if (rc != SEM_OK) return rc;
     int cap_part = std::max(B->cap_ax, B->cap_vec);
+    const int cap_probs_before = B->cap_probs;
     rc = grow(&B->d_probs, &B->cap_probs, std::max(n, 1));
-    if (rc == SEM_OK) {
-        int cap_t = B->cap_probs, cap_f = B->cap_probs;
+    if (rc == SEM_OK && (B->cap_probs != cap_probs_before || !B->tickets || !B->finished_ids)) {
         // tickets (2 per problem) and finished ids follow the problem capacity
         if (B->tickets) dev_free(B->tickets);
         if (B->finished_ids) dev_free(B->finished_ids);
-        B->tickets = static_cast<uint32_t *>(dev_alloc(sizeof(uint32_t) * 2 * size_t(cap_t)));
-        B->finished_ids = static_cast<int32_t *>(dev_alloc(sizeof(int32_t) * (size_t(cap_f) + 1)));
+        B->tickets = static_cast<uint32_t *>(dev_alloc(sizeof(uint32_t) * 2 * size_t(B->cap_probs)));
+        B->finished_ids = static_cast<int32_t *>(dev_alloc(sizeof(int32_t) * (size_t(B->cap_probs) + 1)));
         if (!B->tickets || !B->finished_ids) rc = SEM_ENOMEM;
     }
     if (rc == SEM_OK) rc = grow(&B->d_ax, &B->cap_ax, std::max<int>(int(ax.size()), 1));
@@ -890,7 +905,12 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
                         "batch: item counts");
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
     B->seen_finished = 0;
-    if (B->graph) {
+    // the captured round reads the lists and counts from device memory: it
+    // is captured again only if a buffer moved (grew)
+    const void *bufs[6] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids};
+    const bool same_grids = items_grid(1 << 30, B->n_ax) == B->graph_items[0] &&
+                            items_grid(1 << 30, B->n_vec) == B->graph_items[1];
+    if (B->graph && !(same_grids && std::equal(bufs, bufs + 6, B->graph_bufs))) {
         cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
     }
@@ -940,7 +960,13 @@ static int capture(Batch *B) {
     if (rc == SEM_OK) rc = rc_end;
     if (rc == SEM_OK) rc = cuda_check(cudaGraphInstantiate(&B->graph, g, 0), "batch: instantiate");
     if (g) cudaGraphDestroy(g);
-    if (rc == SEM_OK) B->graph_stream = stream();
+    if (rc == SEM_OK) {
+        B->graph_stream = stream();
+        const void *bufs[6] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids};
+        std::copy(bufs, bufs + 6, B->graph_bufs);
+        B->graph_items[0] = items_grid(1 << 30, B->n_ax);
+        B->graph_items[1] = items_grid(1 << 30, B->n_vec);
+    }
     return rc;
 }
 
@@ -948,6 +974,14 @@ static int capture(Batch *B) {
 // whose inner solve ended (mixed).  Appends the problems that finished during
 // the round (indices into the member list) to *done.
 int batch_round(Batch *B, std::vector<int> *done) {
+    const int rc = batch_round_launch(B);
+    return rc != SEM_OK ? rc : batch_round_finish(B, done);
+}
+
+// A round's launches (init for joining problems, K CG iterations, the
+// refinement phases), issued on the library stream without waiting, so the
+// host can prepare other work (the server admits requests) meanwhile.
+int batch_round_launch(Batch *B) {
     if (B->probs.empty()) return SEM_OK;
     int rc = SEM_OK;
     if (B->any_init) {
@@ -970,7 +1004,13 @@ int batch_round(Batch *B, std::vector<int> *done) {
         if (rc == SEM_OK) rc = launch_flags(B, kFlagClearRefine);
         if (rc != SEM_OK) return rc;
     }
-    rc = read_ctl(B);
+    return SEM_OK;
+}
+
+// Waits for the round and reports the problems that finished in it.
+int batch_round_finish(Batch *B, std::vector<int> *done) {
+    if (B->probs.empty()) return SEM_OK;
+    int rc = read_ctl(B);
     if (rc != SEM_OK) return rc;
     const unsigned nf = B->ctl_host->n_finished;
     if (nf > B->seen_finished) {

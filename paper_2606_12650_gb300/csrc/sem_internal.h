@@ -180,6 +180,12 @@ void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
 void dev_free(void *p);
 cudaStream_t stream();
+// Routes stream() of the calling thread to `s` while the scope lives.
+struct StreamScope {
+    cudaStream_t prev;
+    explicit StreamScope(cudaStream_t s);
+    ~StreamScope();
+};
 void *pinned_slot_alloc();                   // 256 pinned host bytes (CgState mirror); nullptr + error
 void pinned_slot_free(void *p);
 int sm_count();                    // SMs of the current device
@@ -231,6 +237,8 @@ struct Batch;
 Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_outer, int K);
 int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *start, int n);
 int batch_round(Batch *B, std::vector<int> *done);
+int batch_round_launch(Batch *B);                       // the round's launches, no wait
+int batch_round_finish(Batch *B, std::vector<int> *done);   // wait, finished problems
 int batch_results(Batch *B, int64_t *iters, double *res);
 int batch_create(Problem **probs, int n, Batch **out);
 void batch_destroy(Batch *B);

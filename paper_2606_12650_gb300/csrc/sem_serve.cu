@@ -1,16 +1,19 @@
 // sem_serve.cu -- a solve server with continuous batching.
 //
 // Requests (a box mesh and a right-hand side) are queued on the host as they
-// arrive.  Each step of the server (1) admits queued requests in arrival
-// order while the number of active solves and their device memory stay
-// within the server's slot and HBM limits -- admission builds the problem on
-// the device (geometry, mixed-precision factors, right-hand side); (2) if the
-// set of active solves changed, hands the new membership to the batch engine,
-// where joining problems start and running ones keep their state; (3) runs one
-// round of the batch engine (K CG iterations of every active solve in
-// persistent launches, plus refinement for mixed precision); (4) retires the
-// solves that finished: the solution is copied to a compact device buffer,
-// kept there until the client fetches it, and the problem's memory is freed.
+// arrive.  Each step of the server (1) adds the requests admitted during the
+// previous step to the active set and, if the set changed, hands the new
+// membership to the batch engine, where joining problems start and running
+// ones keep their state; (2) launches one round of the batch engine (K CG
+// iterations of every active solve in persistent launches, plus refinement
+// for mixed precision) without waiting for it; (3) while the round runs,
+// admits queued requests in arrival order, within the server's slot and HBM
+// limits, on a stream of its own -- admission builds each problem on the
+// device (geometry, mixed-precision factors, right-hand side), so its host
+// work, allocations and copies overlap the round instead of idling the GPU;
+// (4) waits for the round and retires the solves that finished: the solution
+// is copied to a compact device buffer, kept there until the client fetches
+// it, and the problem's memory is freed.
 // Latency is measured from the request's arrival time to the end of the round
 // in which it finished, on the server's steady clock.  A request's result
 // does not depend on which other requests shared its rounds.  A request whose
@@ -57,6 +60,9 @@ struct Server {
     size_t in_use = 0;
     std::deque<ServeReq *> queue;
     std::vector<ServeReq *> active;
+    std::vector<ServeReq *> pending;  // admitted during the running round; join at the next step
+    std::vector<double *> pending_tmp;  // admission temporaries, freed once the admission stream is idle
+    cudaStream_t adm = nullptr;       // admission work (overlaps the rounds on the library stream)
     std::map<int64_t, ServeReq *> reqs;
     std::vector<int64_t> finished;    // tickets completed since the last drain
     int64_t next_ticket = 1;
@@ -94,7 +100,16 @@ int serve_open(int capacity, double budget_gb, int mode, double tol, double inne
     if (mode < 0 || mode > 2) return set_error(SEM_EARG, "serve_open: mode must be 0, 1 or 2");
     if (K < 1 || K > 4096) return set_error(SEM_EARG, "serve_open: K must be in [1, 4096]");
     if (!(budget_gb > 0.0)) return set_error(SEM_EARG, "serve_open: the HBM budget must be positive");
+    // the admission stream has the highest priority: its small kernels take
+    // SMs as soon as the persistent kernels of a round free any
+    int least = 0, greatest = 0;
+    cudaStream_t adm = nullptr;
+    int rc = cuda_check(cudaDeviceGetStreamPriorityRange(&least, &greatest), "serve_open: priorities");
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaStreamCreateWithPriority(&adm, cudaStreamNonBlocking, greatest), "serve_open: stream");
+    if (rc != SEM_OK) return rc;
     Server *S = new Server();
+    S->adm = adm;
     S->B = batch_new(mode, tol, maxit, inner_tol, 50, K);
     S->mode = mode;
     S->capacity = capacity;
@@ -179,15 +194,17 @@ static int admit(Server *S, ServeReq *q) {
         rc = cuda_check(cudaMemcpyAsync(q->assemble ? f_dev : q->b_dev, q->b.data(), sizeof(double) * q->nL,
                                         cudaMemcpyHostToDevice, stream()), "serve: right-hand side");
     if (rc == SEM_OK && q->assemble) rc = assemble_rhs(q->P, f_dev, q->b_dev);
-    if (f_dev) {
-        cudaStreamSynchronize(stream());
-        dev_free(f_dev);
-    }
-    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "serve: sync");
     if (rc != SEM_OK) {
+        cudaStreamSynchronize(stream());
+        if (f_dev) dev_free(f_dev);
         release_active(q);
         return rc;
     }
+    // no wait here: the right-hand side's source is freed, and the request
+    // joins the batch, after the admission stream is synchronised (next step)
+    if (f_dev) S->pending_tmp.push_back(f_dev);
+    // the host copies above come from q->b / q->verts: pageable memory that
+    // cudaMemcpyAsync has consumed by the time it returns
     std::vector<double>().swap(q->verts);
     std::vector<double>().swap(q->b);
     q->state = 1;
@@ -197,14 +214,16 @@ static int admit(Server *S, ServeReq *q) {
     return SEM_OK;
 }
 
-int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_completed) {
-    int rc = SEM_OK;
-    // (1) admission in arrival order, within the slot and HBM limits
-    while (!S->queue.empty() && int(S->active.size()) < S->capacity) {
+// Admission in arrival order, within the slot and HBM limits, on the
+// server's admission stream; admitted requests wait in `pending`.  Returns
+// the first error that is not the request's own.
+static int admit_queued(Server *S) {
+    StreamScope scope(S->adm);
+    while (!S->queue.empty() && int(S->active.size() + S->pending.size()) < S->capacity) {
         ServeReq *q = S->queue.front();
         if (S->in_use + request_bytes(S->mode, q) > S->budget) break;
-        rc = admit(S, q);
-        if (rc == SEM_ENOMEM && !S->active.empty()) break;   // retry once active solves free memory
+        const int rc = admit(S, q);
+        if (rc == SEM_ENOMEM && !(S->active.empty() && S->pending.empty())) break;   // retry once memory frees up
         if (rc == SEM_EMESH || rc == SEM_EARG || rc == SEM_ENOMEM) {
             // the request itself cannot be served: it fails alone
             S->queue.pop_front();
@@ -219,11 +238,30 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         }
         if (rc != SEM_OK) return rc;
         S->queue.pop_front();
-        S->active.push_back(q);
+        S->pending.push_back(q);
+    }
+    return SEM_OK;
+}
+
+int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_completed) {
+    int rc = SEM_OK;
+    // (1) requests admitted during the previous step join; with nothing
+    // running (a first step, or an idle server) admission runs here
+    if (S->active.empty() && S->pending.empty()) {
+        rc = admit_queued(S);
+        if (rc != SEM_OK) return rc;
+    }
+    if (!S->pending.empty() || !S->pending_tmp.empty()) {
+        rc = cuda_check(cudaStreamSynchronize(S->adm), "serve: admission sync");
+        if (rc != SEM_OK) return rc;
+        for (double *t : S->pending_tmp) dev_free(t);
+        S->pending_tmp.clear();
+        for (ServeReq *q : S->pending) S->active.push_back(q);
+        S->pending.clear();
         S->changed = true;
     }
-    // (2) hand the membership to the batch engine; requests admitted since
-    // the last successful hand-over start, the others keep their state
+    // hand the membership to the batch engine; requests admitted since the
+    // last successful hand-over start, the others keep their state
     if (S->changed) {
         std::vector<Problem *> ps;
         std::vector<const double *> bs;
@@ -238,11 +276,18 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         for (ServeReq *q : S->active) q->fresh = false;
         S->changed = false;
     }
-    // (3) one round for every active solve
+    // (2) launch one round for every active solve; (3) admit meanwhile
+    const bool running = !S->active.empty();
+    if (running) {
+        rc = batch_round_launch(S->B);
+        if (rc != SEM_OK) return rc;
+    }
+    const int rc_admit = admit_queued(S);
+    // (4) wait for the round, retire the finished solves
     std::vector<int> done;
-    if (!S->active.empty()) rc = batch_round(S->B, &done);
+    if (running) rc = batch_round_finish(S->B, &done);
     if (rc != SEM_OK) return rc;
-    // (4) retire the finished solves
+    if (rc_admit != SEM_OK) return rc_admit;
     if (!done.empty()) {
         const double t = serve_now(S);
         std::vector<int64_t> its(S->active.size());
@@ -280,7 +325,7 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         S->changed = true;
     }
     *n_queued = int64_t(S->queue.size());
-    *n_active = int64_t(S->active.size());
+    *n_active = int64_t(S->active.size() + S->pending.size());
     *n_completed = S->completed;
     return SEM_OK;
 }
@@ -336,6 +381,11 @@ int64_t serve_nodes_of(const Server *S, int64_t ticket) {
 void serve_close(Server *S) {
     if (!S) return;
     cudaStreamSynchronize(stream());
+    if (S->adm) {
+        cudaStreamSynchronize(S->adm);
+        for (double *t : S->pending_tmp) dev_free(t);
+        cudaStreamDestroy(S->adm);
+    }
     for (auto &kv : S->reqs) {
         ServeReq *q = kv.second;
         release_active(q);
