@@ -69,8 +69,54 @@ int cuda_check(cudaError_t err, const char *what) {
     return set_error(SEM_ECUDA, buf);
 }
 
+// Device arenas: one allocation from which a group of buffers that live and
+// die together is carved (a served request's problem: ~20 buffers, where each
+// allocation through the allocator hook costs a call into the host runtime
+// that owns the memory).  Inside an ArenaScope, dev_alloc carves 256-byte
+// aligned pieces from the arena and falls back to a real allocation when it
+// is full; dev_free of a carved piece does nothing -- arena_release frees the
+// arena as a whole.
+struct DevArena {
+    unsigned char *base = nullptr;
+    size_t cap = 0, used = 0;
+    std::vector<void *> carved;
+};
+namespace {
+thread_local DevArena *g_arena = nullptr;
+std::map<void *, DevArena *> g_carved;
+}  // namespace
+
+DevArena *arena_new(size_t bytes) {
+    void *p = dev_alloc(bytes);
+    if (!p) return nullptr;
+    DevArena *a = new DevArena();
+    a->base = static_cast<unsigned char *>(p);
+    a->cap = bytes;
+    return a;
+}
+
+void arena_release(DevArena *a) {
+    if (!a) return;
+    for (void *p : a->carved) g_carved.erase(p);
+    dev_free(a->base);
+    delete a;
+}
+
+ArenaScope::ArenaScope(DevArena *a) : prev(g_arena) { g_arena = a; }
+ArenaScope::~ArenaScope() { g_arena = prev; }
+
 void *dev_alloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
+    if (g_arena) {
+        const size_t need = (bytes + 255) / 256 * 256;
+        if (g_arena->used + need <= g_arena->cap) {
+            void *p = g_arena->base + g_arena->used;
+            g_arena->used += need;
+            g_arena->carved.push_back(p);
+            g_carved[p] = g_arena;
+            return p;
+        }
+    }
     if (g.budget && g.in_use + bytes > g.budget) {
         char buf[200];
         snprintf(buf, sizeof buf, "device allocation of %zu bytes exceeds the HBM budget (%zu of %zu in use)",
@@ -103,6 +149,7 @@ void *dev_alloc(size_t bytes) {
 
 void dev_free(void *p) {
     if (!p) return;
+    if (g_carved.count(p)) return;   // released with its arena
     auto it = g.sizes.find(p);
     if (it != g.sizes.end()) {
         g.in_use -= it->second;

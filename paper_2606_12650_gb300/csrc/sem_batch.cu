@@ -1056,6 +1056,35 @@ int batch_results(Batch *B, int64_t *iters, double *res) {
     return SEM_OK;
 }
 
+// The same for the listed members only (a server retiring a few of many).
+int batch_results_of(Batch *B, const std::vector<int> &which, int64_t *iters, double *res) {
+    const size_t m = which.size();
+    std::vector<BatchProb> hp(m);
+    std::vector<CgState> hs(m);
+    int rc = SEM_OK;
+    for (size_t j = 0; j < m && rc == SEM_OK; ++j) {
+        const int k = which[j];
+        if (k < 0 || k >= batch_size(B)) return set_error(SEM_EARG, "batch: member index out of range");
+        rc = cuda_check(cudaMemcpyAsync(&hp[j], B->d_probs + k, sizeof(BatchProb), cudaMemcpyDeviceToHost, stream()),
+                        "batch: results");
+        if (rc == SEM_OK)
+            rc = cuda_check(cudaMemcpyAsync(&hs[j], B->probs[k]->st, sizeof(CgState), cudaMemcpyDeviceToHost, stream()),
+                            "batch: results");
+    }
+    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
+    if (rc != SEM_OK) return rc;
+    for (size_t j = 0; j < m; ++j) {
+        if (B->mode == 0) {
+            iters[j] = hs[j].iter;
+            res[j] = hs[j].rho0 > 0.0 ? std::sqrt(hs[j].rho / hs[j].rho0) : 0.0;
+        } else {
+            iters[j] = hp[j].inner_total;
+            res[j] = hp[j].res;
+        }
+    }
+    return SEM_OK;
+}
+
 // Fixed batch: every problem starts now; rounds until all have finished.
 int batch_solve(Batch *B, const double *b_all, double *x_all, double tol, int maxit, int mode, double inner_tol,
                 int max_outer, int64_t *iters, double *res) {

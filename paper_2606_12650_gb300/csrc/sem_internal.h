@@ -102,7 +102,8 @@ struct Problem {
     double *partials = nullptr;    // after a 16-byte header holding partials_cap (see above)
     int64_t partials_cap = 0;
     CgState *st = nullptr;
-    CgState *st_host = nullptr;    // pinned mirror for polling
+    CgState *st_host = nullptr;    // pinned mirror for polling (pad0: the mesh check's flag at set-up)
+    int32_t *bad_dev = nullptr;    // deferred set-up: the geometry kernel's flag until read
     cudaGraphExec_t graph = nullptr;
     int graph_iters = 0;
     cudaStream_t graph_stream = nullptr;
@@ -179,6 +180,17 @@ void problem_drop_graphs(Problem *P);                     // sem_setup.cu
 // ---- runtime services (sem_api.cu) ---------------------------------------
 void *dev_alloc(size_t bytes);               // nullptr on failure (error set)
 void dev_free(void *p);
+// One allocation carved into many (sem_api.cu): dev_alloc inside an
+// ArenaScope takes pieces of the arena, dev_free of a piece is a no-op,
+// arena_release frees the arena (no piece may be in use on the GPU).
+struct DevArena;
+DevArena *arena_new(size_t bytes);           // nullptr on failure (error set)
+void arena_release(DevArena *a);
+struct ArenaScope {
+    DevArena *prev;
+    explicit ArenaScope(DevArena *a);
+    ~ArenaScope();
+};
 cudaStream_t stream();
 // Routes stream() of the calling thread to `s` while the scope lives.
 struct StreamScope {
@@ -198,7 +210,10 @@ int cuda_check(cudaError_t err, const char *what);
 
 // ---- setup (sem_setup.cu) --------------------------------------------------
 void gll_rule_and_derivative(int N, double *xi, double *w, double *D);   // D row-major (N+1)^2
-int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out);
+// deferred: issue the set-up on stream() without waiting; the caller waits for
+// the stream, then calls problem_check_mesh (SEM_EMESH for an inverted element)
+int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out, bool deferred = false);
+int problem_check_mesh(const Problem *P);
 int problem_maps(Problem *P);                 // gs maps, mask list, weights c (lazy)
 void problem_destroy(Problem *P);
 int launch_nodes(const Problem *P, const double *verts_dev, double *X);
@@ -240,6 +255,7 @@ int batch_round(Batch *B, std::vector<int> *done);
 int batch_round_launch(Batch *B);                       // the round's launches, no wait
 int batch_round_finish(Batch *B, std::vector<int> *done);   // wait, finished problems
 int batch_results(Batch *B, int64_t *iters, double *res);
+int batch_results_of(Batch *B, const std::vector<int> &which, int64_t *iters, double *res);
 int batch_create(Problem **probs, int n, Batch **out);
 void batch_destroy(Batch *B);
 int64_t batch_total_nodes(const Batch *B);

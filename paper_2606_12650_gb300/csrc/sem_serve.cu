@@ -41,6 +41,7 @@ struct ServeReq {
     double arrival = 0.0;             // seconds on the server clock
     bool assemble = false;            // b holds a nodal source f: form mask(QQ^T f) on admission
     Problem *P = nullptr;
+    DevArena *arena = nullptr;        // the request's device buffers, one allocation
     double *b_dev = nullptr;
     double *x_dev = nullptr;          // result, device-resident until fetched
     size_t bytes = 0;                 // device bytes held while active (and its result until fetched)
@@ -169,17 +170,30 @@ static int assemble_rhs(const Problem *P, const double *f, double *b) {
 static void release_active(ServeReq *q) {
     if (q->P) problem_destroy(q->P);
     if (q->b_dev) dev_free(q->b_dev);
+    arena_release(q->arena);
     q->P = nullptr;
     q->b_dev = nullptr;
+    q->arena = nullptr;
 }
 
 static int admit(Server *S, ServeReq *q) {
+    // one allocation for every buffer of the request (problem, factors,
+    // vectors, right-hand side, set-up temporaries), carved by dev_alloc
+    const size_t tmp = sizeof(double) * (q->verts.size() + (q->assemble ? size_t(q->nL) : 0)) + 4096;
+    q->arena = arena_new(request_bytes(S->mode, q) + tmp);
+    if (!q->arena) return SEM_ENOMEM;
+    ArenaScope carve(q->arena);
     double *vdev = static_cast<double *>(dev_alloc(sizeof(double) * q->verts.size()));
-    if (!vdev) return SEM_ENOMEM;
+    if (!vdev) {
+        arena_release(q->arena);
+        q->arena = nullptr;
+        return SEM_ENOMEM;
+    }
     int rc = cuda_check(cudaMemcpyAsync(vdev, q->verts.data(), sizeof(double) * q->verts.size(),
                                         cudaMemcpyHostToDevice, stream()), "serve: vertices");
-    if (rc == SEM_OK) rc = problem_create(q->nx, q->ny, q->nz, q->N, vdev, &q->P);
-    dev_free(vdev);
+    // deferred set-up: nothing here waits for the admission stream; the mesh
+    // check and the temporaries' release follow its synchronisation
+    if (rc == SEM_OK) rc = problem_create(q->nx, q->ny, q->nz, q->N, vdev, &q->P, true);
     if (rc == SEM_OK && S->mode != 0) rc = mixed_prepare(q->P, S->mode == 1 ? kGBF16 : kGF32);
     if (rc == SEM_OK) {
         q->b_dev = static_cast<double *>(dev_alloc(sizeof(double) * q->nL));
@@ -195,13 +209,14 @@ static int admit(Server *S, ServeReq *q) {
                                         cudaMemcpyHostToDevice, stream()), "serve: right-hand side");
     if (rc == SEM_OK && q->assemble) rc = assemble_rhs(q->P, f_dev, q->b_dev);
     if (rc != SEM_OK) {
+        // nothing of the request may still be in flight when its arena goes
         cudaStreamSynchronize(stream());
-        if (f_dev) dev_free(f_dev);
         release_active(q);
         return rc;
     }
-    // no wait here: the right-hand side's source is freed, and the request
+    // no wait here: the set-up temporaries are released, and the request
     // joins the batch, after the admission stream is synchronised (next step)
+    S->pending_tmp.push_back(vdev);
     if (f_dev) S->pending_tmp.push_back(f_dev);
     // the host copies above come from q->b / q->verts: pageable memory that
     // cudaMemcpyAsync has consumed by the time it returns
@@ -256,7 +271,20 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         if (rc != SEM_OK) return rc;
         for (double *t : S->pending_tmp) dev_free(t);
         S->pending_tmp.clear();
-        for (ServeReq *q : S->pending) S->active.push_back(q);
+        for (ServeReq *q : S->pending) {
+            const int mrc = problem_check_mesh(q->P);
+            if (mrc != SEM_OK) {   // an inverted element: this request fails alone
+                release_active(q);
+                S->in_use -= q->bytes;
+                q->state = 3;
+                q->err = mrc;
+                q->t_done = serve_now(S);
+                ++S->completed;
+                S->finished.push_back(q->ticket);
+                continue;
+            }
+            S->active.push_back(q);
+        }
         S->pending.clear();
         S->changed = true;
     }
@@ -290,20 +318,22 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
     if (rc_admit != SEM_OK) return rc_admit;
     if (!done.empty()) {
         const double t = serve_now(S);
-        std::vector<int64_t> its(S->active.size());
-        std::vector<double> res(S->active.size());
-        rc = batch_results(S->B, its.data(), res.data());
+        // results of the finished members only
+        std::vector<int64_t> its(done.size());
+        std::vector<double> res(done.size());
+        rc = batch_results_of(S->B, done, its.data(), res.data());
         if (rc != SEM_OK) return rc;
         std::vector<uint8_t> gone(S->active.size(), 0);
-        for (int k : done) {
+        for (size_t j = 0; j < done.size(); ++j) {
+            const int k = done[j];
             ServeReq *q = S->active[k];
             q->x_dev = static_cast<double *>(dev_alloc(sizeof(double) * q->nL));
             if (!q->x_dev) return SEM_ENOMEM;
             rc = cuda_check(cudaMemcpyAsync(q->x_dev, q->P->x, sizeof(double) * q->nL, cudaMemcpyDeviceToDevice,
                                             stream()), "serve: result");
             if (rc != SEM_OK) return rc;
-            q->iters = its[k];
-            q->res = res[k];
+            q->iters = its[j];
+            q->res = res[j];
             q->t_done = t;
             gone[k] = 1;
         }

@@ -322,7 +322,7 @@ static T *upload(const std::vector<T> &h, int *rc) {
     return d;
 }
 
-int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out) {
+int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Problem **out, bool deferred) {
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return set_error(SEM_EARG, "mesh: nx, ny, nz must be >= 1");
     if (N < 1 || N > kMaxQ - 1) return set_error(SEM_EARG, "mesh: N must be in [1, 9]");
@@ -349,7 +349,8 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
     P->G = static_cast<double *>(dev_alloc(sizeof(double) * 6 * P->nL));
     P->B = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
     int32_t *bad = static_cast<int32_t *>(dev_alloc(sizeof(int32_t) * 4));
-    if (!P->verts || !P->G || !P->B || !bad) rc = SEM_ENOMEM;
+    P->st_host = static_cast<CgState *>(pinned_slot_alloc());
+    if (!P->verts || !P->G || !P->B || !bad || !P->st_host) rc = SEM_ENOMEM;
     if (rc == SEM_OK)
         rc = cuda_check(cudaMemcpyAsync(P->verts, verts_dev, sizeof(double) * 3 * nv, cudaMemcpyDeviceToDevice, stream()),
                         "mesh: vertex copy");
@@ -367,17 +368,21 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         count_launches(1);
         rc = cuda_check(cudaGetLastError(), "geom_kernel");
     }
-    if (rc == SEM_OK) {
-        int32_t hbad = 0;
-        rc = cuda_check(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, stream()), "mesh: flag");
-        if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
-        if (rc == SEM_OK && hbad != 0x7fffffff) {
-            char msg[128];
-            snprintf(msg, sizeof msg, "mesh: non-positive Jacobian at local node %d", hbad - 1);
-            rc = set_error(SEM_EMESH, msg);
-        }
+    // the first non-positive Jacobian's node (or 0x7fffffff) into the pinned
+    // state mirror; deferred: read by problem_check_mesh once the stream is idle
+    if (rc == SEM_OK)
+        rc = cuda_check(cudaMemcpyAsync(&P->st_host->pad0, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, stream()),
+                        "mesh: flag");
+    if (rc == SEM_OK && !deferred) {
+        rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
+        if (rc == SEM_OK) rc = problem_check_mesh(P);
     }
-    if (bad) dev_free(bad);
+    if (bad) {
+        if (deferred && rc == SEM_OK)
+            P->bad_dev = bad;   // freed by problem_destroy, after the flag was read
+        else
+            dev_free(bad);
+    }
     if (rc == SEM_OK) {
         P->x = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
         P->r = static_cast<double *>(dev_alloc(sizeof(double) * P->nL));
@@ -390,10 +395,6 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
         if (!P->x || !P->r || !P->p || !P->w || !P->partials || !P->st) rc = SEM_ENOMEM;
     }
     if (rc == SEM_OK) rc = prepare_ax(P);
-    if (rc == SEM_OK) {
-        P->st_host = static_cast<CgState *>(pinned_slot_alloc());
-        if (!P->st_host) rc = SEM_ENOMEM;
-    }
     if (rc == SEM_OK) rc = cuda_check(cudaMemsetAsync(P->st, 0, sizeof(CgState), stream()), "mesh: state");
     if (rc == SEM_OK)
         rc = cuda_check(cudaMemsetAsync(group_tickets(P->partials, P->partials_cap), 0,
@@ -405,13 +406,24 @@ int problem_create(int nx, int ny, int nz, int N, const double *verts_dev, Probl
                                         sizeof(int64_t), cudaMemcpyHostToDevice, stream()),
                         "mesh: partials header");
     }
-    if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
+    if (rc == SEM_OK && !deferred) rc = cuda_check(cudaStreamSynchronize(stream()), "mesh: sync");
     if (rc != SEM_OK) {
+        if (deferred) cudaStreamSynchronize(stream());   // nothing of P may still be in flight
         problem_destroy(P);
         return rc;
     }
     *out = P;
     return SEM_OK;
+}
+
+// SEM_EMESH if the geometry kernel found a non-positive Jacobian (the flag
+// problem_create copied to the state mirror); the stream must be idle.
+int problem_check_mesh(const Problem *P) {
+    const int32_t hbad = P->st_host->pad0;
+    if (hbad == 0x7fffffff) return SEM_OK;
+    char msg[128];
+    snprintf(msg, sizeof msg, "mesh: non-positive Jacobian at local node %d", hbad - 1);
+    return set_error(SEM_EMESH, msg);
 }
 
 // Sorted-segment gather-scatter maps, mask list and multiplicity weights,
@@ -451,6 +463,7 @@ void problem_destroy(Problem *P) {
     if (P->graph) cudaGraphExecDestroy(P->graph);
     if (P->graph_pcg) cudaGraphExecDestroy(P->graph_pcg);
     if (P->dinv) dev_free(P->dinv);
+    if (P->bad_dev) dev_free(P->bad_dev);
     mixed_release(P);
     dw_release(P);
     if (P->partials) dev_free(reinterpret_cast<unsigned char *>(P->partials) - 16);
