@@ -94,6 +94,14 @@ struct DwAcc {
 __device__ __forceinline__ void acc_square(double &a, double r) { a = fma(r, r, a); }
 __device__ __forceinline__ void acc_square(float &a, float r) { a = fmaf(r, r, a); }
 __device__ __forceinline__ void acc_square(DwAcc &a, double r) { a.v = dw_add_square(a.v, r); }
+// Jacobi PCG: acc + d r^2 (= r . (d r) with z = d r), FP64 or double-word
+__device__ __forceinline__ void acc_weighted_square(double &a, double d, double r) { a = fma(r, d * r, a); }
+__device__ __forceinline__ void acc_weighted_square(DwAcc &a, double d, double r) {
+    a.v = dw_add_weighted_square(a.v, d, r);
+}
+__device__ __forceinline__ void acc_merge(double &a, double b) { a += b; }
+__device__ __forceinline__ void acc_merge(float &a, float b) { a += b; }
+__device__ __forceinline__ void acc_merge(DwAcc &a, const DwAcc &b) { a.v = dw_add(a.v, b.v); }
 __device__ __forceinline__ double acc_value(double a) { return a; }
 __device__ __forceinline__ double acc_value(float a) { return double(a); }
 __device__ __forceinline__ double acc_value(const DwAcc &a) { return dw_to_double(a.v); }
@@ -303,8 +311,8 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
             if (owner_row && !((v == 0) && has_lo)) {
                 if constexpr (PRE) {
                     // <r, M^-1 r> for beta and <r, r> for the stop test
-                    acc = fma(Acc(rv[v]), Acc(dv[v] * rv[v]), acc);
-                    rr = fma(Acc(rv[v]), Acc(rv[v]), rr);
+                    acc_weighted_square(acc, dv[v], rv[v]);
+                    acc_square(rr, rv[v]);
                 } else {
                     acc_square(acc, rv[v]);
                 }
@@ -313,7 +321,7 @@ __device__ __forceinline__ void update_vec(T *__restrict__ x, T *__restrict__ r,
     }
     if (!DX) vstore<T, V>(x + l0, xv);
     vstore<T, V>(r + l0, rv);
-    if constexpr (PRE) *acc_rr += rr;
+    if constexpr (PRE) acc_merge(*acc_rr, rr);
 }
 
 // Row-class mapping of update vectors to threads: a warp takes the same row

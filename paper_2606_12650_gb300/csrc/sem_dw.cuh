@@ -112,4 +112,15 @@ __device__ __forceinline__ dwf dw_add_square(dwf acc, double r) {
     return {s, __fadd_rn(t, __fadd_rn(e, f))};
 }
 
+// acc + d r^2 for FP64 d, r (the Jacobi-weighted <r, M^-1 r> term):
+// r^2 = p + (e + 2hl) as in dw_add_square, then times d's double-word form.
+__device__ __forceinline__ dwf dw_add_weighted_square(dwf acc, double d, double r) {
+    const dwf v = dw_from_double(r);
+    const dwf w = dw_from_double(d);
+    const float p = __fmul_rn(v.h, v.h);
+    const float e = __fmaf_rn(v.h, v.h, -p);
+    const dwf sq = {p, __fmaf_rn(__fmul_rn(2.0f, v.h), v.l, e)};
+    return dw_fma(w, sq, acc);
+}
+
 }  // namespace sem

@@ -129,17 +129,19 @@ __global__ void __launch_bounds__(256) pcg_update_kernel(double *__restrict__ x,
     constexpr int V = UpdVec<NQ, double>::value;
     using RM = RowMap<NQ, V>;
     const double alpha = st->alpha;
-    double rz = 0.0, rr = 0.0;
+    // both reductions accumulated in double-word FP32 per thread (the
+    // recurrences stay FP64): GB300's FP64 pipe runs at 1/64 rate
+    DwAcc rz = acc_zero<DwAcc>(), rr = acc_zero<DwAcc>();
     const int E = nL / RM::NP;
     const int ntask = RM::tasks(E);
     const int lane = threadIdx.x & 31;
     const int nwarps = int(gridDim.x * blockDim.x) >> 5;
     for (int task = int(blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarps) {
         const int l0 = RM::l0(task, lane, E);
-        if (l0 >= 0) update_vec<NQ, V, double, double, true, true>(x, r, p, w, l0, bd, alpha, rz, dinv, &rr);
+        if (l0 >= 0) update_vec<NQ, V, double, DwAcc, true, true>(x, r, p, w, l0, bd, alpha, rz, dinv, &rr);
     }
-    const double s0 = block_sum(rz, red);
-    const double s1 = block_sum(rr, red);
+    const double s0 = block_sum(acc_value(rz), red);
+    const double s1 = block_sum(acc_value(rr), red);
     if (publish_partial2(s0, s1, partials, &st->ticket_up)) {
         double rho_new, rr_new;
         finish_partials2(partials, int(gridDim.x), &st->ticket_up, red, &rho_new, &rr_new);
