@@ -1,18 +1,21 @@
 // sem_batch.cu -- many independent Poisson problems of different sizes and
-// orders solved together: each CG phase is ONE persistent launch over all
-// problems, replayed from a CUDA graph.
+// orders solved together: each CG phase is a few persistent launches over all
+// problems (one per order present for the operator, one for the vector
+// update), replayed from a CUDA graph.
 //
 // Work lists.  Every problem is cut into operator items (~16384 local nodes:
 // several passes of a 256-thread block) and vector items (row-aligned runs of
 // ~16384 local nodes).  A persistent kernel's CTAs take items from a global
-// counter (dynamic load balance across problems of very different cost); a
-// device-side switch on N dispatches to the body compiled for that order.
-// The operator body and the elements per pass follow the per-order tuner's
-// table for the batch's precision: the line body (sem_ax_lines.cuh), in
-// double-word arithmetic for FP64 batches where the table chose that variant
-// (sem_ax_dw.cuh), or the column body, passes of 256 / (N+1)^2 elements.  Items of problems whose solve finished
-// are dropped from the lists between rounds (their order within a problem,
-// and so its reductions, never change).
+// counter (dynamic load balance across problems of very different cost).
+// The operator list keeps each order's items together, and each order has
+// its own kernel, compiled for that order and body with the body inlined;
+// the vector kernel switches on N on the device.  The operator body and the
+// elements per pass follow the per-order tuner's table for the batch's
+// precision: the line body (sem_ax_lines.cuh), in double-word arithmetic for
+// FP64 batches where the table chose that variant (sem_ax_dw.cuh), or the
+// column body, passes of 256 / (N+1)^2 elements.  Items of problems whose
+// solve finished are dropped from the lists between rounds (the items of one
+// problem stay together and in order, so its reductions never change).
 //
 // Per-problem reductions.  Each item writes one partial (fixed-order block
 // tree) to its own slot; the problem's last item to finish (per-problem
@@ -34,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -87,11 +91,19 @@ struct BatchQueue {
 
 enum BatchQ : int { kQAx = 0, kQVec = 1, kNumQ = 2 };
 
+// Operator bodies of a batch: every member of one order takes the same one.
+enum AxBody : int { kBodyColumns = 0, kBodyLines = 1, kBodyDW = 2, kBodyNone = -1 };
+constexpr int kOrders = kMaxQ - 1;  // N+1 = 2 .. kMaxQ
+
 struct BatchCtl {
-    BatchQueue q[kNumQ];
+    BatchQueue q[kNumQ];            // [kQVec]: the vector phases' queue
     unsigned n_finished;            // entries in the finished list
     int n_items[kNumQ];             // items in the current (compacted) lists
     unsigned pad;
+    // the operator list holds the items of each order together (order N+1 =
+    // 2 first); each order's launch takes its range through its own queue
+    BatchQueue q_ax[kOrders];
+    int ax_first[kOrders], ax_count[kOrders];
 };
 
 struct Batch {
@@ -104,7 +116,9 @@ struct Batch {
     // every member's items as built by batch_set, with its range in them; a
     // member whose solve finished is left out of the device lists (`gone`)
     std::vector<BatchItem> ax_all, vec_all;
-    std::vector<int> ax_first_all, vec_first_all;
+    std::vector<int> ax_first_all, ax_count_all, vec_first_all;
+    int ord_body[kOrders];          // operator body per order (kBodyNone: no member of that order)
+    int ord_count[kOrders];         // operator items per order in the device list now
     std::vector<uint8_t> gone;
     int cap_probs = 0, cap_ax = 0, cap_vec = 0;
     BatchProb *d_probs = nullptr;
@@ -116,7 +130,6 @@ struct Batch {
     BatchCtl *ctl_host = nullptr;
     unsigned seen_finished = 0;
     bool any_init = false;
-    int grid_ax64 = 0, grid_ax32 = 0;   // resident CTAs of the operator launches
     cudaGraphExec_t graph = nullptr;
     cudaStream_t graph_stream = nullptr;
     // the buffers the captured round reads and its grids; the graph stays
@@ -124,6 +137,14 @@ struct Batch {
     // (membership changes only rewrite the lists' contents and counts)
     const void *graph_bufs[6] = {};
     int graph_items[2] = {0, 0};    // power-of-two ceilings of the item counts at capture
+    int ord_ranges[2 * kOrders];    // host copy of the device per-order (first, count) ranges
+    int graph_ord[kOrders] = {};    // per order: the captured launch's grid ceiling and body (0: none)
+    int64_t graph_launches = 0;     // kernel launches in one replay
+    // side streams and events that fork the per-order operator launches into
+    // parallel branches of the captured round (the tail of one order's launch
+    // overlaps the others)
+    cudaStream_t side[kOrders] = {};
+    cudaEvent_t fork = nullptr, join[kOrders] = {};
 };
 
 template <int NQ>
@@ -131,15 +152,13 @@ struct BEpb {
     static constexpr int value = kBatchThreads / (NQ * NQ);
 };
 
-template <typename T>
-size_t batch_ax_smem() {
-    size_t m = 0;
-#define SEM_BS(Q)                                          \
-    m = std::max(m, AxShape<Q, BEpb<Q>::value, T>::SMEM);  \
-    m = std::max(m, LineShape::smem(Q, BEpb<Q>::value, int(sizeof(T))));
-    SEM_BS(2) SEM_BS(3) SEM_BS(4) SEM_BS(5) SEM_BS(6) SEM_BS(7) SEM_BS(8) SEM_BS(9) SEM_BS(10)
-#undef SEM_BS
-    return m;
+// Dynamic shared memory of one order's operator body: the column body's
+// slabs, or the line body's three regions (FP64-sized for the double-word
+// body, whose values are FP32 pairs).
+template <int NQ, typename T, int BODY>
+inline size_t batch_ax_smem() {
+    return BODY == kBodyColumns ? AxShape<NQ, BEpb<NQ>::value, T>::SMEM
+                                : LineShape::smem(NQ, BEpb<NQ>::value, BODY == kBodyDW ? 8 : int(sizeof(T)));
 }
 
 // Derivative matrices of every order in constant memory: D depends only on
@@ -223,13 +242,14 @@ __device__ __forceinline__ bool item_partial(double v0, double *part, int it, ui
 // ------------------------------------------------------------------ operator
 // One item of order NQ: `count` elements from `first`, taken in groups of
 // what one pass of the block holds (`group` elements), so that an item's
-// fixed costs -- the queue ticket, the call, the block reduction of its
-// partial -- are shared by several groups.  Kept out of line so that each
-// order's body gets its own register allocation (inlined into one switch, the
-// nine bodies share and exhaust the register file).  *phase is the mbarrier
-// phase of the next completion; each group uses one.
+// fixed costs -- the queue ticket, the block reduction of its partial -- are
+// shared by several groups.  Each order and body has its own kernel, with
+// the body inlined: as out-of-line calls from one kernel over all orders,
+// the call convention's register saves and the caller's per-call-site
+// stack spilled on every group.  *phase is the mbarrier phase of the next
+// completion; each group uses one.
 template <int NQ, typename T, typename GT, bool CG>
-__device__ __noinline__ bool batch_ax_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
+__device__ __forceinline__ bool batch_ax_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
                                            int count, T *regA, uint64_t *bar, uint32_t *phase, int32_t *status,
                                            T *pt) {
     constexpr int GR = BEpb<NQ>::value;
@@ -249,7 +269,7 @@ __device__ __noinline__ bool batch_ax_item(const T *xin, T *yout, T *pv, const G
 }
 
 template <int NQ, typename T, typename GT, bool CG>
-__device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
+__device__ __forceinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, const GT *G, T beta, int64_t first,
                                               int count, int group, T *regA, uint64_t *bar, uint32_t *phase,
                                               int32_t *status, T *pt) {
     constexpr int GM = kGLoad;   // factors loaded at use: the register prefetch would not fit 4 CTAs per SM
@@ -272,7 +292,7 @@ __device__ __noinline__ bool batch_lines_item(const T *xin, T *yout, T *pv, cons
 
 // The double-word line body (FP64 batches): same passes as batch_lines_item.
 template <int NQ, bool CG>
-__device__ __noinline__ bool batch_dw_item(const double *xin, double *yout, double *pv, const float *Gdw, double beta,
+__device__ __forceinline__ bool batch_dw_item(const double *xin, double *yout, double *pv, const float *Gdw, double beta,
                                            int64_t first, int count, int group, double *regA, uint64_t *bar,
                                            uint32_t *phase, int32_t *status, double *pt) {
     double acc = 0.0;
@@ -293,13 +313,15 @@ __device__ __noinline__ bool batch_dw_item(const double *xin, double *yout, doub
 
 // mode: 0 = FP64 CG (p = r + beta p, w = A p), 1 = FP64 plain (w = A x),
 //       2 = FP32 inner CG on the FP32 vectors
-// FP32 items are HBM-bound: 4 CTAs per SM (<= 64 registers) for latency
-// hiding; FP64 items are FP64-pipe bound and keep the column body's registers.
-template <typename T, typename GT, int MODE>
-__global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2) batch_ax_kernel(BatchProb *probs, const BatchItem *items,
-                                                                 double *part, uint32_t *tickets, BatchCtl *ctl,
-                                                                 int32_t *status) {
+// One order's items (N+1 = NQ), one body.  FP32 items are HBM-bound: 4 CTAs
+// per SM (<= 64 registers) for latency hiding; FP64 items keep the FP64
+// bodies' registers (2 CTAs per SM).
+template <typename T, typename GT, int MODE, int NQ, int BODY>
+__global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2)
+    batch_ax_kernel(BatchProb *probs, const BatchItem *items, double *part, uint32_t *tickets, BatchCtl *ctl,
+                    int32_t *status) {
     constexpr bool CG = MODE != 1;
+    static_assert(BODY != kBodyDW || std::is_same<T, double>::value, "the double-word body is FP64");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red[32];
     __shared__ int s_item;
@@ -308,11 +330,13 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2) batch_a
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     uint32_t phase = 0;
-    BatchQueue *q = &ctl->q[kQAx];
-    const int nitems = ctl->n_items[kQAx];
+    BatchQueue *q = &ctl->q_ax[NQ - 2];
+    const int first = ctl->ax_first[NQ - 2];
+    const int nitems = ctl->ax_count[NQ - 2];
     while (true) {
-        const int it = next_item(q, &s_item);
-        if (it >= nitems) break;
+        const int k = next_item(q, &s_item);
+        if (k >= nitems) break;
+        const int it = first + k;
         const BatchItem item = items[it];
         BatchProb &P = probs[item.prob];
         CgState *st = MODE == 2 ? P.st_in : P.st;
@@ -324,28 +348,17 @@ __global__ void __launch_bounds__(kBatchThreads, sizeof(T) == 4 ? 4 : 2) batch_a
         if (MODE == 0) { xin = reinterpret_cast<const T *>(P.r); yout = reinterpret_cast<T *>(P.w); pv = reinterpret_cast<T *>(P.p); }
         else if (MODE == 1) { xin = reinterpret_cast<const T *>(P.x); yout = reinterpret_cast<T *>(P.w); pv = nullptr; }
         else { xin = reinterpret_cast<const T *>(P.r32); yout = reinterpret_cast<T *>(P.w32); pv = reinterpret_cast<T *>(P.p32); }
-        const GT *G = prob_G<GT>(P);
         T pt = T(0);
-        bool ok = true;
-        switch (item.nq) {
-#define SEM_BAX(Q)                                                                                       \
-    case Q:                                                                                              \
-        if constexpr (std::is_same<T, double>::value) {                                                  \
-            if (item.dw) {                                                                               \
-                ok = batch_dw_item<Q, CG>(xin, yout, pv, P.Gdw, beta, item.first, item.count, item.group,  \
-                                          regA, bar, &phase, status, &pt);                               \
-                break;                                                                                   \
-            }                                                                                            \
-        }                                                                                                \
-        ok = item.group ? batch_lines_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,   \
-                                                         item.group, regA, bar, &phase, status, &pt)       \
-                        : batch_ax_item<Q, T, GT, CG>(xin, yout, pv, G, beta, item.first, item.count,      \
-                                                      regA, bar, &phase, status, &pt);                     \
-        break;
-            SEM_BAX(2) SEM_BAX(3) SEM_BAX(4) SEM_BAX(5) SEM_BAX(6) SEM_BAX(7) SEM_BAX(8) SEM_BAX(9) SEM_BAX(10)
-#undef SEM_BAX
-            default: break;
-        }
+        bool ok;
+        if constexpr (BODY == kBodyDW)
+            ok = batch_dw_item<NQ, CG>(xin, yout, pv, P.Gdw, beta, item.first, item.count, item.group, regA, bar,
+                                       &phase, status, &pt);
+        else if constexpr (BODY == kBodyLines)
+            ok = batch_lines_item<NQ, T, GT, CG>(xin, yout, pv, prob_G<GT>(P), beta, item.first, item.count,
+                                                 item.group, regA, bar, &phase, status, &pt);
+        else
+            ok = batch_ax_item<NQ, T, GT, CG>(xin, yout, pv, prob_G<GT>(P), beta, item.first, item.count, regA, bar,
+                                              &phase, status, &pt);
         if (!ok) return;  // timed out: the status word reports it; the solve is abandoned
         if (CG) {
             const double bs = block_sum(double(pt), red);
@@ -577,14 +590,128 @@ static int items_grid(int resident, int n) {
     return std::max(1, std::min(resident, p));
 }
 
+// One order's operator kernel: its shared-memory limit set and its
+// resident CTAs computed on first use (batch_set, before any capture), then
+// launched over a grid for `count` items.
+template <typename T, typename GT, int MODE, int NQ, int BODY>
+struct BaxLaunch {
+    static int resident(int *out) {
+        static int grid = 0;
+        if (!grid) {
+            const void *k = reinterpret_cast<const void *>(batch_ax_kernel<T, GT, MODE, NQ, BODY>);
+            const size_t sm = batch_ax_smem<NQ, T, BODY>();
+            int rc = cuda_check(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)),
+                                "batch: shared-memory attribute");
+            if (rc == SEM_OK) rc = batch_grid(k, sm, &grid);
+            if (rc != SEM_OK) return rc;
+        }
+        *out = grid;
+        return SEM_OK;
+    }
+    static int launch(Batch *B, int count) {
+        int res = 0;
+        const int rc = resident(&res);
+        if (rc != SEM_OK) return rc;
+        batch_ax_kernel<T, GT, MODE, NQ, BODY>
+            <<<unsigned(items_grid(res, count)), kBatchThreads, batch_ax_smem<NQ, T, BODY>(), stream()>>>(
+                B->d_probs, B->d_ax, B->part, B->tickets, B->ctl, status_word());
+        count_launches(1);
+        return cuda_check(cudaGetLastError(), "batch_ax_kernel");
+    }
+};
+
+// Dispatch on the order and body (prepare only, or launch for `count`
+// items).  The double-word body exists for FP64 CG batches only.
+template <typename T, typename GT, int MODE, int NQ>
+static int bax_order(Batch *B, int body, int count, bool launch) {
+    int res = 0;
+    switch (body) {
+        case kBodyColumns:
+            return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyColumns>::launch(B, count)
+                          : BaxLaunch<T, GT, MODE, NQ, kBodyColumns>::resident(&res);
+        case kBodyLines:
+            return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyLines>::launch(B, count)
+                          : BaxLaunch<T, GT, MODE, NQ, kBodyLines>::resident(&res);
+        case kBodyDW:
+            if constexpr (MODE == 0)
+                return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyDW>::launch(B, count)
+                              : BaxLaunch<T, GT, MODE, NQ, kBodyDW>::resident(&res);
+            [[fallthrough]];
+        default: return set_error(SEM_EARG, "batch: no such operator body for this precision");
+    }
+}
+
 template <typename T, typename GT, int MODE>
-static int launch_bax(Batch *B, int grid) {
-    const size_t sm = batch_ax_smem<T>();
-    const int g = items_grid(grid, B->n_ax);
-    batch_ax_kernel<T, GT, MODE><<<unsigned(g), kBatchThreads, sm, stream()>>>(B->d_probs, B->d_ax, B->part,
-                                                                             B->tickets, B->ctl, status_word());
-    count_launches(1);
-    return cuda_check(cudaGetLastError(), "batch_ax_kernel");
+static int bax(Batch *B, int nq, int body, int count, bool launch) {
+    switch (nq) {
+        case 2: return bax_order<T, GT, MODE, 2>(B, body, count, launch);
+        case 3: return bax_order<T, GT, MODE, 3>(B, body, count, launch);
+        case 4: return bax_order<T, GT, MODE, 4>(B, body, count, launch);
+        case 5: return bax_order<T, GT, MODE, 5>(B, body, count, launch);
+        case 6: return bax_order<T, GT, MODE, 6>(B, body, count, launch);
+        case 7: return bax_order<T, GT, MODE, 7>(B, body, count, launch);
+        case 8: return bax_order<T, GT, MODE, 8>(B, body, count, launch);
+        case 9: return bax_order<T, GT, MODE, 9>(B, body, count, launch);
+        case 10: return bax_order<T, GT, MODE, 10>(B, body, count, launch);
+        default: return set_error(SEM_EARG, "batch: unsupported order");
+    }
+}
+
+// The operator phase of one precision: one launch per order present, in
+// sequence, or (parallel) the first on the current stream and the others on
+// side streams forked from it and joined back.
+template <typename T, typename GT, int MODE>
+static int launch_bax(Batch *B, bool parallel = false) {
+    const cudaStream_t s = stream();
+    bool first = true;
+    // the fork point: what precedes the phase on the current stream
+    int rc = parallel ? cuda_check(cudaEventRecord(B->fork, s), "batch: fork") : SEM_OK;
+    for (int o = 0; o < kOrders && rc == SEM_OK; ++o) {
+        if (B->ord_body[o] == kBodyNone) continue;
+        if (!parallel || first) {
+            rc = bax<T, GT, MODE>(B, o + 2, B->ord_body[o], B->ord_count[o], true);
+            first = false;
+            continue;
+        }
+        rc = cuda_check(cudaStreamWaitEvent(B->side[o], B->fork, 0), "batch: fork");
+        if (rc == SEM_OK) {
+            StreamScope on(B->side[o]);
+            rc = bax<T, GT, MODE>(B, o + 2, B->ord_body[o], B->ord_count[o], true);
+        }
+        if (rc == SEM_OK) rc = cuda_check(cudaEventRecord(B->join[o], B->side[o]), "batch: join");
+        if (rc == SEM_OK) rc = cuda_check(cudaStreamWaitEvent(s, B->join[o], 0), "batch: join");
+    }
+    return rc;
+}
+
+// Side streams and events of the parallel operator phase (made once, outside
+// any capture).
+static int make_side_streams(Batch *B) {
+    if (B->fork) return SEM_OK;
+    int rc = cuda_check(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming), "batch: event");
+    for (int o = 0; o < kOrders && rc == SEM_OK; ++o) {
+        rc = cuda_check(cudaStreamCreateWithFlags(&B->side[o], cudaStreamNonBlocking), "batch: stream");
+        if (rc == SEM_OK) rc = cuda_check(cudaEventCreateWithFlags(&B->join[o], cudaEventDisableTiming), "batch: event");
+    }
+    return rc;
+}
+
+// Every operator kernel this batch's rounds launch, prepared before capture.
+static int prepare_bax(Batch *B) {
+    for (int o = 0; o < kOrders; ++o) {
+        const int body = B->ord_body[o];
+        if (body == kBodyNone) continue;
+        int rc;
+        if (B->mode == 0) {
+            rc = bax<double, double, 0>(B, o + 2, body, 0, false);
+        } else {
+            rc = B->mode == 1 ? bax<float, __nv_bfloat16, 2>(B, o + 2, body, 0, false)
+                              : bax<float, float, 2>(B, o + 2, body, 0, false);
+            if (rc == SEM_OK) rc = bax<double, double, 1>(B, o + 2, body, 0, false);
+        }
+        if (rc != SEM_OK) return rc;
+    }
+    return SEM_OK;
 }
 
 // Resident CTAs of one vector phase's kernel (the phases differ in
@@ -650,29 +777,12 @@ static int batch_attrs(Batch *B) {
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E64, e64, sizeof e64), "batch: even-odd table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_E32, e32, sizeof e32), "batch: even-odd table");
         if (rc == SEM_OK) rc = cuda_check(cudaMemcpyToSymbol(c_EDW, edw, sizeof edw), "batch: even-odd table");
-        const int a = int(batch_ax_smem<double>()), f = int(batch_ax_smem<float>());
-        if (rc == SEM_OK)
-            rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 0>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, a), "batch attr");
-        if (rc == SEM_OK)
-            rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<double, double, 1>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, a), "batch attr");
-        if (rc == SEM_OK)
-            rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<float, __nv_bfloat16, 2>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, f), "batch attr");
-        if (rc == SEM_OK)
-            rc = cuda_check(cudaFuncSetAttribute(batch_ax_kernel<float, float, 2>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, f), "batch attr");
         if (rc != SEM_OK) return rc;
         done = true;
     }
-    int rc = batch_grid(reinterpret_cast<const void *>(batch_ax_kernel<double, double, 0>), batch_ax_smem<double>(),
-                        &B->grid_ax64);
-    if (rc == SEM_OK)
-        rc = batch_grid(reinterpret_cast<const void *>(batch_ax_kernel<float, __nv_bfloat16, 2>),
-                        batch_ax_smem<float>(), &B->grid_ax32);
+    (void)B;
     int g = 0;
-    if (rc == SEM_OK) rc = vec_grid<kVecUpdate64>(&g);
+    int rc = vec_grid<kVecUpdate64>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecUpdate32>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecInit64>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecInner>(&g);
@@ -701,6 +811,25 @@ static int read_ctl(Batch *B) {
     return rc;
 }
 
+// Per-order ranges of the operator list to the device (the caller syncs).
+static int upload_order_ranges(Batch *B, const int *ord_first) {
+    for (int o = 0; o < kOrders; ++o) {
+        B->ord_ranges[o] = ord_first[o];
+        B->ord_ranges[kOrders + o] = B->ord_count[o];
+    }
+    static_assert(offsetof(BatchCtl, ax_count) == offsetof(BatchCtl, ax_first) + kOrders * sizeof(int),
+                  "ranges are copied as one block");
+    return cuda_check(cudaMemcpyAsync(B->ctl->ax_first, B->ord_ranges, sizeof B->ord_ranges, cudaMemcpyHostToDevice,
+                                      stream()), "batch: order ranges");
+}
+
+// What a captured round's operator launches depend on: per order, its body
+// and the power-of-two ceiling of its item count (0: no launch).
+static void order_signature(const Batch *B, int *out) {
+    for (int o = 0; o < kOrders; ++o)
+        out[o] = B->ord_body[o] == kBodyNone ? 0 : 4 * items_grid(1 << 30, B->ord_count[o]) + B->ord_body[o] + 1;
+}
+
 // New item ranges of the members after a compaction (ax_first, ax_count,
 // vec_first, vec_count per member; a finished member gets empty ranges).
 __global__ void batch_relist_kernel(BatchProb *probs, const int4 *ranges, int n) {
@@ -721,18 +850,24 @@ __global__ void batch_relist_kernel(BatchProb *probs, const int4 *ranges, int n)
 static int compact(Batch *B) {
     const int n = int(B->probs.size());
     std::vector<BatchItem> ax, vec;
-    std::vector<int4> ranges(n);
-    for (int k = 0; k < n; ++k) {
-        const Problem *P = B->probs[k];
-        (void)P;
-        const int a0 = B->ax_first_all[k], a1 = B->ax_first_all[k + 1];
-        const int v0 = B->vec_first_all[k], v1 = B->vec_first_all[k + 1];
-        if (B->gone[k]) {
-            ranges[k] = make_int4(0, 0, 0, 0);
-            continue;
+    std::vector<int4> ranges(n, make_int4(0, 0, 0, 0));
+    int ord_first[kOrders];
+    for (int o = 0; o < kOrders; ++o) {   // operator items: by order, members in order
+        ord_first[o] = int(ax.size());
+        for (int k = 0; k < n; ++k) {
+            if (B->gone[k] || B->probs[k]->nq - 2 != o) continue;
+            const int a0 = B->ax_first_all[k], na = B->ax_count_all[k];
+            ranges[k].x = int(ax.size());
+            ranges[k].y = na;
+            ax.insert(ax.end(), B->ax_all.begin() + a0, B->ax_all.begin() + a0 + na);
         }
-        ranges[k] = make_int4(int(ax.size()), a1 - a0, int(vec.size()), v1 - v0);
-        ax.insert(ax.end(), B->ax_all.begin() + a0, B->ax_all.begin() + a1);
+        B->ord_count[o] = int(ax.size()) - ord_first[o];
+    }
+    for (int k = 0; k < n; ++k) {          // vector items: members in order
+        if (B->gone[k]) continue;
+        const int v0 = B->vec_first_all[k], v1 = B->vec_first_all[k + 1];
+        ranges[k].z = int(vec.size());
+        ranges[k].w = v1 - v0;
         vec.insert(vec.end(), B->vec_all.begin() + v0, B->vec_all.begin() + v1);
     }
     int rc = SEM_OK;
@@ -755,6 +890,7 @@ static int compact(Batch *B) {
     if (rc == SEM_OK)
         rc = cuda_check(cudaMemcpyAsync(B->ctl->n_items, counts, sizeof counts, cudaMemcpyHostToDevice, stream()),
                         "batch: item counts");
+    if (rc == SEM_OK) rc = upload_order_ranges(B, ord_first);
     // the host copies above come from pageable memory; finish them before
     // the vectors go out of scope
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
@@ -774,6 +910,8 @@ Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_oute
     B->inner_tol = inner_tol;
     B->max_outer = max_outer;
     B->K = K;
+    std::fill(B->ord_body, B->ord_body + kOrders, int(kBodyNone));
+    std::fill(B->ord_count, B->ord_count + kOrders, 0);
     return B;
 }
 
@@ -800,6 +938,9 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     }
     std::vector<BatchProb> hp(n);
     std::vector<BatchItem> ax, vec;
+    std::vector<BatchItem> by_ord[kOrders];   // operator items of each order, members in order
+    int ord_body[kOrders];
+    std::fill(ord_body, ord_body + kOrders, int(kBodyNone));
     bool any_init = false;
     for (int k = 0; k < n && rc == SEM_OK; ++k) {
         Problem *P = probs[k];
@@ -844,17 +985,37 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
         const int group = full;
         const int np = P->nq * P->nq * P->nq;
         const int per_item = group * std::max(1, kAxItemNodes / (np * group));
-        q.ax_first = int(ax.size());
+        const int o = P->nq - 2;
+        const int body = dw ? kBodyDW : (lines ? kBodyLines : kBodyColumns);
+        if (ord_body[o] != kBodyNone && ord_body[o] != body) {
+            rc = set_error(SEM_EARG, "batch: members of one order with different operator bodies");
+            break;
+        }
+        ord_body[o] = body;
+        std::vector<BatchItem> &oa = by_ord[o];
+        q.ax_first = int(oa.size());   // within its order's items; placed below
         for (int64_t e = 0; e < P->E; e += per_item)
-            ax.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(per_item, P->E - e)), lines ? group : 0,
+            oa.push_back(BatchItem{k, P->nq, e, int(std::min<int64_t>(per_item, P->E - e)), lines ? group : 0,
                                    dw ? 1 : 0});
-        q.ax_count = int(ax.size()) - q.ax_first;
+        q.ax_count = int(oa.size()) - q.ax_first;
         const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
         q.vec_first = int(vec.size());
         for (int64_t l = 0; l < P->nL; l += chunk)
             vec.push_back(BatchItem{k, P->nq, l, int(std::min<int64_t>(chunk, P->nL - l)), 0});
         q.vec_count = int(vec.size()) - q.vec_first;
     }
+    if (rc != SEM_OK) return rc;
+    // the operator list: each order's items together, orders ascending
+    int ord_first[kOrders];
+    for (int o = 0; o < kOrders; ++o) {
+        ord_first[o] = int(ax.size());
+        ax.insert(ax.end(), by_ord[o].begin(), by_ord[o].end());
+    }
+    for (int k = 0; k < n; ++k) hp[k].ax_first += ord_first[probs[k]->nq - 2];
+    std::copy(ord_body, ord_body + kOrders, B->ord_body);
+    for (int o = 0; o < kOrders; ++o) B->ord_count[o] = int(by_ord[o].size());
+    rc = prepare_bax(B);
+    if (rc == SEM_OK) rc = make_side_streams(B);
     if (rc != SEM_OK) return rc;
     int cap_part = std::max(B->cap_ax, B->cap_vec);
     const int cap_probs_before = B->cap_probs;
@@ -876,13 +1037,14 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     B->n_vec = int(vec.size());
     B->ax_all = ax;
     B->vec_all = vec;
-    B->ax_first_all.assign(n + 1, 0);
+    B->ax_first_all.assign(n, 0);
+    B->ax_count_all.assign(n, 0);
     B->vec_first_all.assign(n + 1, 0);
     for (int k = 0; k < n; ++k) {
         B->ax_first_all[k] = hp[k].ax_first;
+        B->ax_count_all[k] = hp[k].ax_count;
         B->vec_first_all[k] = hp[k].vec_first;
     }
-    B->ax_first_all[n] = B->n_ax;
     B->vec_first_all[n] = B->n_vec;
     B->gone.assign(n, 0);
     B->any_init = any_init;
@@ -903,12 +1065,15 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     if (rc == SEM_OK)
         rc = cuda_check(cudaMemcpyAsync(B->ctl->n_items, counts, sizeof counts, cudaMemcpyHostToDevice, stream()),
                         "batch: item counts");
+    if (rc == SEM_OK) rc = upload_order_ranges(B, ord_first);
     if (rc == SEM_OK) rc = cuda_check(cudaStreamSynchronize(stream()), "batch: sync");
     B->seen_finished = 0;
     // the captured round reads the lists and counts from device memory: it
     // is captured again only if a buffer moved (grew)
     const void *bufs[6] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids};
-    const bool same_grids = items_grid(1 << 30, B->n_ax) == B->graph_items[0] &&
+    int ord_now[kOrders];
+    order_signature(B, ord_now);
+    const bool same_grids = std::equal(ord_now, ord_now + kOrders, B->graph_ord) &&
                             items_grid(1 << 30, B->n_vec) == B->graph_items[1];
     if (B->graph && !(same_grids && std::equal(bufs, bufs + 6, B->graph_bufs))) {
         cudaGraphExecDestroy(B->graph);
@@ -920,6 +1085,11 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
 void batch_destroy(Batch *B) {
     if (!B) return;
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (int o = 0; o < kOrders; ++o) {
+        if (B->side[o]) cudaStreamDestroy(B->side[o]);
+        if (B->join[o]) cudaEventDestroy(B->join[o]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
     void *ptrs[] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids, B->ctl};
     for (void *q : ptrs)
         if (q) dev_free(q);
@@ -945,17 +1115,19 @@ static int capture(Batch *B) {
     cudaGraph_t g = nullptr;
     int rc = cuda_check(cudaStreamBeginCapture(stream(), cudaStreamCaptureModeThreadLocal), "batch: capture");
     if (rc != SEM_OK) return rc;
+    int orders = 0;
+    for (int o = 0; o < kOrders; ++o) orders += B->ord_body[o] != kBodyNone;
     for (int k = 0; k < B->K && rc == SEM_OK; ++k) {
         if (B->mode == 0) {
-            rc = launch_bax<double, double, 0>(B, B->grid_ax64);
+            rc = launch_bax<double, double, 0>(B, true);
             if (rc == SEM_OK) rc = launch_bvec<kVecUpdate64>(B);
         } else {
-            rc = B->mode == 1 ? launch_bax<float, __nv_bfloat16, 2>(B, B->grid_ax32)
-                              : launch_bax<float, float, 2>(B, B->grid_ax32);
+            rc = B->mode == 1 ? launch_bax<float, __nv_bfloat16, 2>(B, true) : launch_bax<float, float, 2>(B, true);
             if (rc == SEM_OK) rc = launch_bvec<kVecUpdate32>(B);
         }
     }
-    count_launches(-2 * int64_t(B->K));
+    B->graph_launches = int64_t(B->K) * (orders + 1);
+    count_launches(-B->graph_launches);
     const int rc_end = cuda_check(cudaStreamEndCapture(stream(), &g), "batch: end capture");
     if (rc == SEM_OK) rc = rc_end;
     if (rc == SEM_OK) rc = cuda_check(cudaGraphInstantiate(&B->graph, g, 0), "batch: instantiate");
@@ -966,6 +1138,7 @@ static int capture(Batch *B) {
         std::copy(bufs, bufs + 6, B->graph_bufs);
         B->graph_items[0] = items_grid(1 << 30, B->n_ax);
         B->graph_items[1] = items_grid(1 << 30, B->n_vec);
+        order_signature(B, B->graph_ord);
     }
     return rc;
 }
@@ -994,11 +1167,11 @@ int batch_round_launch(Batch *B) {
     rc = capture(B);
     if (rc == SEM_OK) rc = cuda_check(cudaGraphLaunch(B->graph, stream()), "batch: graph launch");
     if (rc != SEM_OK) return rc;
-    count_launches(2 * int64_t(B->K));
+    count_launches(B->graph_launches);
     if (B->mode != 0) {
         rc = launch_flags(B, kFlagMarkRefine);
         if (rc == SEM_OK) rc = launch_bvec<kVecCorrect>(B);
-        if (rc == SEM_OK) rc = launch_bax<double, double, 1>(B, B->grid_ax64);
+        if (rc == SEM_OK) rc = launch_bax<double, double, 1>(B);
         if (rc == SEM_OK) rc = launch_bvec<kVecResidual>(B);
         if (rc == SEM_OK) rc = launch_bvec<kVecInner>(B);
         if (rc == SEM_OK) rc = launch_flags(B, kFlagClearRefine);
