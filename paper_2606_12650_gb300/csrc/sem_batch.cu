@@ -104,6 +104,9 @@ struct BatchCtl {
     // 2 first); each order's launch takes its range through its own queue
     BatchQueue q_ax[kOrders];
     int ax_first[kOrders], ax_count[kOrders];
+    // the vector list likewise, for the per-order update launches
+    int vec_first[kOrders], vec_count[kOrders];
+    BatchQueue q_vec[kOrders];
 };
 
 struct Batch {
@@ -116,14 +119,18 @@ struct Batch {
     // every member's items as built by batch_set, with its range in them; a
     // member whose solve finished is left out of the device lists (`gone`)
     std::vector<BatchItem> ax_all, vec_all;
-    std::vector<int> ax_first_all, ax_count_all, vec_first_all;
+    std::vector<int> ax_first_all, ax_count_all, vec_first_all, vec_count_all;
     int ord_body[kOrders];          // operator body per order (kBodyNone: no member of that order)
     int ord_count[kOrders];         // operator items per order in the device list now
+    int ord_vcount[kOrders];        // vector items per order in the device list now
     std::vector<uint8_t> gone;
     int cap_probs = 0, cap_ax = 0, cap_vec = 0;
     BatchProb *d_probs = nullptr;
     BatchItem *d_ax = nullptr, *d_vec = nullptr;
-    double *part = nullptr;         // one slot per item
+    double *part = nullptr;         // one slot per operator item
+    double *part_vec = nullptr;     // one slot per vector item (an order's update may run beside
+                                    // another order's operator)
+    int cap_part = 0, cap_part_vec = 0;
     uint32_t *tickets = nullptr;    // per problem: [ax, vec]
     int32_t *finished_ids = nullptr;
     BatchCtl *ctl = nullptr;
@@ -135,10 +142,10 @@ struct Batch {
     // the buffers the captured round reads and its grids; the graph stays
     // valid while the buffers stay in place and the grids stay the same
     // (membership changes only rewrite the lists' contents and counts)
-    const void *graph_bufs[6] = {};
+    const void *graph_bufs[7] = {};
     int graph_items[2] = {0, 0};    // power-of-two ceilings of the item counts at capture
-    int ord_ranges[2 * kOrders];    // host copy of the device per-order (first, count) ranges
-    int graph_ord[kOrders] = {};    // per order: the captured launch's grid ceiling and body (0: none)
+    int ord_ranges[4 * kOrders];    // host copy of the device per-order ranges (operator, vector)
+    int graph_ord[2 * kOrders] = {};  // per order: the captured launches' grid ceilings and body (0: none)
     int64_t graph_launches = 0;     // kernel launches in one replay
     // side streams and events that fork the per-order operator launches into
     // parallel branches of the captured round (the tail of one order's launch
@@ -422,23 +429,30 @@ __device__ __forceinline__ double residual_node(double *r, const double *b, cons
     return bn.owner ? rv * rv : 0.0;
 }
 
+// The CG update of one item (FP64 CG, or the FP32 inner CG), returning the
+// block's threads' <r, r> partials.
+template <int NQ, int MODE>
+__device__ __forceinline__ double vec_update_item(BatchProb &P, CgState *st, int64_t first, int count) {
+    using T = typename std::conditional<MODE == kVecUpdate64, double, float>::type;
+    constexpr int V = UpdVec<NQ, T>::value;
+    const BoxDims bd = P.bd;   // in registers for the whole item
+    T *x = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.x) : reinterpret_cast<T *>(P.d32);
+    T *r = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.r) : reinterpret_cast<T *>(P.r32);
+    const T *p = MODE == kVecUpdate64 ? reinterpret_cast<const T *>(P.p) : reinterpret_cast<const T *>(P.p32);
+    const T *w = MODE == kVecUpdate64 ? reinterpret_cast<const T *>(P.w) : reinterpret_cast<const T *>(P.w32);
+    const T alpha = T(st->alpha);
+    T a = T(0);
+    for (int v = threadIdx.x; v < count / V; v += blockDim.x)
+        update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, bd, alpha, a);
+    return double(a);
+}
+
 template <int NQ, int MODE>
 __device__ __noinline__ double vec_item_body(BatchProb &P, CgState *st, int64_t first, int count) {
     double acc = 0.0;
     const int tid = threadIdx.x;
     if (MODE == kVecUpdate64 || MODE == kVecUpdate32) {
-        using T = typename std::conditional<MODE == kVecUpdate64, double, float>::type;
-        constexpr int V = UpdVec<NQ, T>::value;
-        const BoxDims bd = P.bd;   // in registers for the whole item
-        T *x = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.x) : reinterpret_cast<T *>(P.d32);
-        T *r = MODE == kVecUpdate64 ? reinterpret_cast<T *>(P.r) : reinterpret_cast<T *>(P.r32);
-        const T *p = MODE == kVecUpdate64 ? reinterpret_cast<const T *>(P.p) : reinterpret_cast<const T *>(P.p32);
-        const T *w = MODE == kVecUpdate64 ? reinterpret_cast<const T *>(P.w) : reinterpret_cast<const T *>(P.w32);
-        const T alpha = T(st->alpha);
-        T a = T(0);
-        for (int v = tid; v < count / V; v += blockDim.x)
-            update_vec<NQ, V, T, T>(x, r, p, w, int(first) + v * V, bd, alpha, a);
-        acc = double(a);
+        acc = vec_update_item<NQ, MODE>(P, st, first, count);
     } else if (MODE == kVecInit64) {
         // <b, b> over global nodes (each counted at its first copy)
         for (int v = tid; v < count; v += blockDim.x) {
@@ -557,6 +571,39 @@ __global__ void __launch_bounds__(kBatchThreads, MODE == kVecUpdate32 ? 4 : 3) b
     leave_queue(q);
 }
 
+// The CG update phase for one order's items (its range of the vector list),
+// the body inlined like the operator's.
+constexpr int kUpd32Blocks = 4;   // CTAs per SM of the FP32 update (<= 64 registers)
+template <int MODE, int NQ>
+__global__ void __launch_bounds__(kBatchThreads, MODE == kVecUpdate32 ? kUpd32Blocks : 3)
+    batch_update_kernel(BatchProb *probs, const BatchItem *items, double *part, uint32_t *tickets, BatchCtl *ctl,
+                        int32_t *finished_ids) {
+    static_assert(MODE == kVecUpdate64 || MODE == kVecUpdate32, "update phases only");
+    __shared__ double red[32];
+    __shared__ int s_item;
+    BatchQueue *q = &ctl->q_vec[NQ - 2];
+    const int first = ctl->vec_first[NQ - 2];
+    const int nitems = ctl->vec_count[NQ - 2];
+    while (true) {
+        const int k = next_item(q, &s_item);
+        if (k >= nitems) break;
+        const int it = first + k;
+        const BatchItem item = items[it];
+        BatchProb &P = probs[item.prob];
+        CgState *st = MODE == kVecUpdate32 ? P.st_in : P.st;
+        if (st->done || P.finished) continue;
+        const double acc = vec_update_item<NQ, MODE>(P, st, item.first, item.count);
+        const double bs = block_sum(acc, red);
+        double tot;
+        if (!item_partial(bs, part, it, &tickets[2 * item.prob + 1], P.vec_first, P.vec_count, red, &tot) ||
+            threadIdx.x != 0)
+            continue;
+        cg_close_iteration(st, tot);
+        if (MODE == kVecUpdate64 && st->done) finish_problem(P, item.prob, ctl, finished_ids);
+    }
+    leave_queue(q);
+}
+
 // Per-problem flag updates between phases (one thread per problem).
 enum FlagOp : int { kFlagClearInit = 0, kFlagMarkRefine = 1, kFlagClearRefine = 2 };
 
@@ -657,11 +704,11 @@ static int bax(Batch *B, int nq, int body, int count, bool launch) {
     }
 }
 
-// The operator phase of one precision: one launch per order present, in
-// sequence, or (parallel) the first on the current stream and the others on
-// side streams forked from it and joined back.
-template <typename T, typename GT, int MODE>
-static int launch_bax(Batch *B, bool parallel = false) {
+// One launch per order present (fn(o) launches order o on the current
+// stream), in sequence, or (parallel) the first on the current stream and
+// the others on side streams forked from it and joined back.
+template <typename F>
+static int launch_orders(Batch *B, bool parallel, F &&fn) {
     const cudaStream_t s = stream();
     bool first = true;
     // the fork point: what precedes the phase on the current stream
@@ -669,19 +716,62 @@ static int launch_bax(Batch *B, bool parallel = false) {
     for (int o = 0; o < kOrders && rc == SEM_OK; ++o) {
         if (B->ord_body[o] == kBodyNone) continue;
         if (!parallel || first) {
-            rc = bax<T, GT, MODE>(B, o + 2, B->ord_body[o], B->ord_count[o], true);
+            rc = fn(o);
             first = false;
             continue;
         }
         rc = cuda_check(cudaStreamWaitEvent(B->side[o], B->fork, 0), "batch: fork");
         if (rc == SEM_OK) {
             StreamScope on(B->side[o]);
-            rc = bax<T, GT, MODE>(B, o + 2, B->ord_body[o], B->ord_count[o], true);
+            rc = fn(o);
         }
         if (rc == SEM_OK) rc = cuda_check(cudaEventRecord(B->join[o], B->side[o]), "batch: join");
         if (rc == SEM_OK) rc = cuda_check(cudaStreamWaitEvent(s, B->join[o], 0), "batch: join");
     }
     return rc;
+}
+
+// The operator phase of one precision.
+template <typename T, typename GT, int MODE>
+static int launch_bax(Batch *B, bool parallel = false) {
+    return launch_orders(B, parallel, [B](int o) {
+        return bax<T, GT, MODE>(B, o + 2, B->ord_body[o], B->ord_count[o], true);
+    });
+}
+
+// One order's update kernel: resident CTAs on first use, then launched.
+template <int MODE, int NQ>
+struct UpdLaunch {
+    static int resident(int *out) {
+        static int grid = 0;
+        if (!grid) {
+            const int rc = batch_grid(reinterpret_cast<const void *>(batch_update_kernel<MODE, NQ>), 0, &grid);
+            if (rc != SEM_OK) return rc;
+        }
+        *out = grid;
+        return SEM_OK;
+    }
+    static int launch(Batch *B, int count) {
+        int res = 0;
+        const int rc = resident(&res);
+        if (rc != SEM_OK) return rc;
+        batch_update_kernel<MODE, NQ><<<unsigned(items_grid(res, count)), kBatchThreads, 0, stream()>>>(
+            B->d_probs, B->d_vec, B->part_vec, B->tickets, B->ctl, B->finished_ids);
+        count_launches(1);
+        return cuda_check(cudaGetLastError(), "batch_update_kernel");
+    }
+};
+
+template <int MODE>
+static int upd(Batch *B, int nq, int count, bool launch) {
+    int res = 0;
+    switch (nq) {
+#define SEM_UPD(Q) \
+    case Q: return launch ? UpdLaunch<MODE, Q>::launch(B, count) : UpdLaunch<MODE, Q>::resident(&res);
+        SEM_UPD(2) SEM_UPD(3) SEM_UPD(4) SEM_UPD(5) SEM_UPD(6) SEM_UPD(7) SEM_UPD(8) SEM_UPD(9) SEM_UPD(10)
+#undef SEM_UPD
+        default: return set_error(SEM_EARG, "batch: unsupported order");
+    }
 }
 
 // Side streams and events of the parallel operator phase (made once, outside
@@ -704,10 +794,12 @@ static int prepare_bax(Batch *B) {
         int rc;
         if (B->mode == 0) {
             rc = bax<double, double, 0>(B, o + 2, body, 0, false);
+            if (rc == SEM_OK) rc = upd<kVecUpdate64>(B, o + 2, 0, false);
         } else {
             rc = B->mode == 1 ? bax<float, __nv_bfloat16, 2>(B, o + 2, body, 0, false)
                               : bax<float, float, 2>(B, o + 2, body, 0, false);
             if (rc == SEM_OK) rc = bax<double, double, 1>(B, o + 2, body, 0, false);
+            if (rc == SEM_OK) rc = upd<kVecUpdate32>(B, o + 2, 0, false);
         }
         if (rc != SEM_OK) return rc;
     }
@@ -734,7 +826,7 @@ static int launch_bvec(Batch *B) {
     const int rcg = vec_grid<MODE>(&grid);
     if (rcg != SEM_OK) return rcg;
     const int g = items_grid(grid, B->n_vec);
-    batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->part, B->tickets,
+    batch_vec_kernel<MODE><<<unsigned(g), kBatchThreads, 0, stream()>>>(B->d_probs, B->d_vec, B->part_vec, B->tickets,
                                                                        B->ctl, B->finished_ids, A);
     count_launches(1);
     return cuda_check(cudaGetLastError(), "batch_vec_kernel");
@@ -782,9 +874,7 @@ static int batch_attrs(Batch *B) {
     }
     (void)B;
     int g = 0;
-    int rc = vec_grid<kVecUpdate64>(&g);
-    if (rc == SEM_OK) rc = vec_grid<kVecUpdate32>(&g);
-    if (rc == SEM_OK) rc = vec_grid<kVecInit64>(&g);
+    int rc = vec_grid<kVecInit64>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecInner>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecCorrect>(&g);
     if (rc == SEM_OK) rc = vec_grid<kVecResidual>(&g);
@@ -811,23 +901,31 @@ static int read_ctl(Batch *B) {
     return rc;
 }
 
-// Per-order ranges of the operator list to the device (the caller syncs).
+// Per-order ranges of the operator and vector lists to the device (ord_first:
+// the operator firsts, then the vector firsts; the caller syncs).
 static int upload_order_ranges(Batch *B, const int *ord_first) {
     for (int o = 0; o < kOrders; ++o) {
         B->ord_ranges[o] = ord_first[o];
         B->ord_ranges[kOrders + o] = B->ord_count[o];
+        B->ord_ranges[2 * kOrders + o] = ord_first[kOrders + o];
+        B->ord_ranges[3 * kOrders + o] = B->ord_vcount[o];
     }
-    static_assert(offsetof(BatchCtl, ax_count) == offsetof(BatchCtl, ax_first) + kOrders * sizeof(int),
+    static_assert(offsetof(BatchCtl, ax_count) == offsetof(BatchCtl, ax_first) + kOrders * sizeof(int) &&
+                      offsetof(BatchCtl, vec_first) == offsetof(BatchCtl, ax_first) + 2 * kOrders * sizeof(int) &&
+                      offsetof(BatchCtl, vec_count) == offsetof(BatchCtl, ax_first) + 3 * kOrders * sizeof(int),
                   "ranges are copied as one block");
     return cuda_check(cudaMemcpyAsync(B->ctl->ax_first, B->ord_ranges, sizeof B->ord_ranges, cudaMemcpyHostToDevice,
                                       stream()), "batch: order ranges");
 }
 
-// What a captured round's operator launches depend on: per order, its body
-// and the power-of-two ceiling of its item count (0: no launch).
+// What a captured round's launches depend on: per order, its operator body
+// and the power-of-two ceilings of its item counts (0: no launches).
 static void order_signature(const Batch *B, int *out) {
-    for (int o = 0; o < kOrders; ++o)
-        out[o] = B->ord_body[o] == kBodyNone ? 0 : 4 * items_grid(1 << 30, B->ord_count[o]) + B->ord_body[o] + 1;
+    for (int o = 0; o < kOrders; ++o) {
+        const bool on = B->ord_body[o] != kBodyNone;
+        out[o] = on ? 4 * items_grid(1 << 30, B->ord_count[o]) + B->ord_body[o] + 1 : 0;
+        out[kOrders + o] = on ? items_grid(1 << 30, B->ord_vcount[o]) : 0;
+    }
 }
 
 // New item ranges of the members after a compaction (ax_first, ax_count,
@@ -851,24 +949,20 @@ static int compact(Batch *B) {
     const int n = int(B->probs.size());
     std::vector<BatchItem> ax, vec;
     std::vector<int4> ranges(n, make_int4(0, 0, 0, 0));
-    int ord_first[kOrders];
-    for (int o = 0; o < kOrders; ++o) {   // operator items: by order, members in order
+    int ord_first[2 * kOrders];
+    for (int o = 0; o < kOrders; ++o) {   // by order, members in order
         ord_first[o] = int(ax.size());
+        ord_first[kOrders + o] = int(vec.size());
         for (int k = 0; k < n; ++k) {
             if (B->gone[k] || B->probs[k]->nq - 2 != o) continue;
             const int a0 = B->ax_first_all[k], na = B->ax_count_all[k];
-            ranges[k].x = int(ax.size());
-            ranges[k].y = na;
+            const int v0 = B->vec_first_all[k], nv = B->vec_count_all[k];
+            ranges[k] = make_int4(int(ax.size()), na, int(vec.size()), nv);
             ax.insert(ax.end(), B->ax_all.begin() + a0, B->ax_all.begin() + a0 + na);
+            vec.insert(vec.end(), B->vec_all.begin() + v0, B->vec_all.begin() + v0 + nv);
         }
         B->ord_count[o] = int(ax.size()) - ord_first[o];
-    }
-    for (int k = 0; k < n; ++k) {          // vector items: members in order
-        if (B->gone[k]) continue;
-        const int v0 = B->vec_first_all[k], v1 = B->vec_first_all[k + 1];
-        ranges[k].z = int(vec.size());
-        ranges[k].w = v1 - v0;
-        vec.insert(vec.end(), B->vec_all.begin() + v0, B->vec_all.begin() + v1);
+        B->ord_vcount[o] = int(vec.size()) - ord_first[kOrders + o];
     }
     int rc = SEM_OK;
     int4 *d_ranges = static_cast<int4 *>(dev_alloc(sizeof(int4) * size_t(std::max(n, 1))));
@@ -912,6 +1006,7 @@ Batch *batch_new(int mode, double tol, int maxit, double inner_tol, int max_oute
     B->K = K;
     std::fill(B->ord_body, B->ord_body + kOrders, int(kBodyNone));
     std::fill(B->ord_count, B->ord_count + kOrders, 0);
+    std::fill(B->ord_vcount, B->ord_vcount + kOrders, 0);
     return B;
 }
 
@@ -939,6 +1034,7 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     std::vector<BatchProb> hp(n);
     std::vector<BatchItem> ax, vec;
     std::vector<BatchItem> by_ord[kOrders];   // operator items of each order, members in order
+    std::vector<BatchItem> by_ord_v[kOrders]; // vector items likewise
     int ord_body[kOrders];
     std::fill(ord_body, ord_body + kOrders, int(kBodyNone));
     bool any_init = false;
@@ -999,25 +1095,33 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
                                    dw ? 1 : 0});
         q.ax_count = int(oa.size()) - q.ax_first;
         const int64_t chunk = std::max<int64_t>(P->nq, (kVecItemNodes / P->nq) * P->nq);
-        q.vec_first = int(vec.size());
+        std::vector<BatchItem> &ov = by_ord_v[o];
+        q.vec_first = int(ov.size());  // within its order's items; placed below
         for (int64_t l = 0; l < P->nL; l += chunk)
-            vec.push_back(BatchItem{k, P->nq, l, int(std::min<int64_t>(chunk, P->nL - l)), 0});
-        q.vec_count = int(vec.size()) - q.vec_first;
+            ov.push_back(BatchItem{k, P->nq, l, int(std::min<int64_t>(chunk, P->nL - l)), 0});
+        q.vec_count = int(ov.size()) - q.vec_first;
     }
     if (rc != SEM_OK) return rc;
-    // the operator list: each order's items together, orders ascending
-    int ord_first[kOrders];
+    // the lists: each order's items together, orders ascending
+    int ord_first[2 * kOrders];
     for (int o = 0; o < kOrders; ++o) {
         ord_first[o] = int(ax.size());
         ax.insert(ax.end(), by_ord[o].begin(), by_ord[o].end());
+        ord_first[kOrders + o] = int(vec.size());
+        vec.insert(vec.end(), by_ord_v[o].begin(), by_ord_v[o].end());
     }
-    for (int k = 0; k < n; ++k) hp[k].ax_first += ord_first[probs[k]->nq - 2];
+    for (int k = 0; k < n; ++k) {
+        hp[k].ax_first += ord_first[probs[k]->nq - 2];
+        hp[k].vec_first += ord_first[kOrders + probs[k]->nq - 2];
+    }
     std::copy(ord_body, ord_body + kOrders, B->ord_body);
-    for (int o = 0; o < kOrders; ++o) B->ord_count[o] = int(by_ord[o].size());
+    for (int o = 0; o < kOrders; ++o) {
+        B->ord_count[o] = int(by_ord[o].size());
+        B->ord_vcount[o] = int(by_ord_v[o].size());
+    }
     rc = prepare_bax(B);
     if (rc == SEM_OK) rc = make_side_streams(B);
     if (rc != SEM_OK) return rc;
-    int cap_part = std::max(B->cap_ax, B->cap_vec);
     const int cap_probs_before = B->cap_probs;
     rc = grow(&B->d_probs, &B->cap_probs, std::max(n, 1));
     if (rc == SEM_OK && (B->cap_probs != cap_probs_before || !B->tickets || !B->finished_ids)) {
@@ -1030,7 +1134,8 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     }
     if (rc == SEM_OK) rc = grow(&B->d_ax, &B->cap_ax, std::max<int>(int(ax.size()), 1));
     if (rc == SEM_OK) rc = grow(&B->d_vec, &B->cap_vec, std::max<int>(int(vec.size()), 1));
-    if (rc == SEM_OK) rc = grow(&B->part, &cap_part, std::max(B->cap_ax, B->cap_vec));
+    if (rc == SEM_OK) rc = grow(&B->part, &B->cap_part, B->cap_ax);
+    if (rc == SEM_OK) rc = grow(&B->part_vec, &B->cap_part_vec, B->cap_vec);
     if (rc != SEM_OK) return rc;
     B->probs.assign(probs, probs + n);
     B->n_ax = int(ax.size());
@@ -1039,13 +1144,14 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     B->vec_all = vec;
     B->ax_first_all.assign(n, 0);
     B->ax_count_all.assign(n, 0);
-    B->vec_first_all.assign(n + 1, 0);
+    B->vec_first_all.assign(n, 0);
+    B->vec_count_all.assign(n, 0);
     for (int k = 0; k < n; ++k) {
         B->ax_first_all[k] = hp[k].ax_first;
         B->ax_count_all[k] = hp[k].ax_count;
         B->vec_first_all[k] = hp[k].vec_first;
+        B->vec_count_all[k] = hp[k].vec_count;
     }
-    B->vec_first_all[n] = B->n_vec;
     B->gone.assign(n, 0);
     B->any_init = any_init;
     if (n)
@@ -1070,12 +1176,11 @@ int batch_set(Batch *B, Problem **probs, const double *const *b, const uint8_t *
     B->seen_finished = 0;
     // the captured round reads the lists and counts from device memory: it
     // is captured again only if a buffer moved (grew)
-    const void *bufs[6] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids};
-    int ord_now[kOrders];
+    const void *bufs[7] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->part_vec, B->tickets, B->finished_ids};
+    int ord_now[2 * kOrders];
     order_signature(B, ord_now);
-    const bool same_grids = std::equal(ord_now, ord_now + kOrders, B->graph_ord) &&
-                            items_grid(1 << 30, B->n_vec) == B->graph_items[1];
-    if (B->graph && !(same_grids && std::equal(bufs, bufs + 6, B->graph_bufs))) {
+    const bool same_grids = std::equal(ord_now, ord_now + 2 * kOrders, B->graph_ord);
+    if (B->graph && !(same_grids && std::equal(bufs, bufs + 7, B->graph_bufs))) {
         cudaGraphExecDestroy(B->graph);
         B->graph = nullptr;
     }
@@ -1090,7 +1195,7 @@ void batch_destroy(Batch *B) {
         if (B->join[o]) cudaEventDestroy(B->join[o]);
     }
     if (B->fork) cudaEventDestroy(B->fork);
-    void *ptrs[] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids, B->ctl};
+    void *ptrs[] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->part_vec, B->tickets, B->finished_ids, B->ctl};
     for (void *q : ptrs)
         if (q) dev_free(q);
     if (B->ctl_host) cudaFreeHost(B->ctl_host);
@@ -1117,16 +1222,25 @@ static int capture(Batch *B) {
     if (rc != SEM_OK) return rc;
     int orders = 0;
     for (int o = 0; o < kOrders; ++o) orders += B->ord_body[o] != kBodyNone;
-    for (int k = 0; k < B->K && rc == SEM_OK; ++k) {
-        if (B->mode == 0) {
-            rc = launch_bax<double, double, 0>(B, true);
-            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate64>(B);
-        } else {
-            rc = B->mode == 1 ? launch_bax<float, __nv_bfloat16, 2>(B, true) : launch_bax<float, float, 2>(B, true);
-            if (rc == SEM_OK) rc = launch_bvec<kVecUpdate32>(B);
+    // each order's problems are independent of the others': its K
+    // iterations form one chain of (operator, update) launches, the orders'
+    // chains parallel branches of the round
+    rc = launch_orders(B, true, [B](int o) {
+        const int nq = o + 2, body = B->ord_body[o], na = B->ord_count[o], nv = B->ord_vcount[o];
+        int r = SEM_OK;
+        for (int k = 0; k < B->K && r == SEM_OK; ++k) {
+            if (B->mode == 0) {
+                r = bax<double, double, 0>(B, nq, body, na, true);
+                if (r == SEM_OK) r = upd<kVecUpdate64>(B, nq, nv, true);
+            } else {
+                r = B->mode == 1 ? bax<float, __nv_bfloat16, 2>(B, nq, body, na, true)
+                                 : bax<float, float, 2>(B, nq, body, na, true);
+                if (r == SEM_OK) r = upd<kVecUpdate32>(B, nq, nv, true);
+            }
         }
-    }
-    B->graph_launches = int64_t(B->K) * (orders + 1);
+        return r;
+    });
+    B->graph_launches = int64_t(B->K) * 2 * orders;
     count_launches(-B->graph_launches);
     const int rc_end = cuda_check(cudaStreamEndCapture(stream(), &g), "batch: end capture");
     if (rc == SEM_OK) rc = rc_end;
@@ -1134,8 +1248,8 @@ static int capture(Batch *B) {
     if (g) cudaGraphDestroy(g);
     if (rc == SEM_OK) {
         B->graph_stream = stream();
-        const void *bufs[6] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->tickets, B->finished_ids};
-        std::copy(bufs, bufs + 6, B->graph_bufs);
+        const void *bufs[7] = {B->d_probs, B->d_ax, B->d_vec, B->part, B->part_vec, B->tickets, B->finished_ids};
+        std::copy(bufs, bufs + 7, B->graph_bufs);
         B->graph_items[0] = items_grid(1 << 30, B->n_ax);
         B->graph_items[1] = items_grid(1 << 30, B->n_vec);
         order_signature(B, B->graph_ord);
