@@ -466,10 +466,10 @@ def run_ours(a):
     if not a.no_serve and rank == 0:
         from paper_2606_12650_gb300.serve import sweep
         rates = [float(r) for r in a.serve_rates.split(",")]
-        rows = sweep(rates, a.serve_requests, seed=5, mode=1, budget_gb=40.0, K=8, tol=a.tol)
+        rows = sweep(rates, a.serve_requests, seed=5, mode=1, budget_gb=40.0, K=16, tol=a.tol)
         served = {"workload": f"Poisson arrivals, {a.serve_requests} requests per rate, E log-uniform [8, 8192] "
                               f"(near-cubic boxes), N in {{5,7}}, jitter 5%, random source, tol {a.tol:g}, "
-                              "mixed precision (BF16 G), 40 GB admission budget, 8 CG iterations per round",
+                              "mixed precision (BF16 G), 40 GB admission budget, 16 CG iterations per round",
                   "rates": rows, "closed_loop": run_served_ceiling(a, stream, sem, torch)}
 
     # ---- the paper's own protocol: GDOF/s against E for N = 4, 6, 8

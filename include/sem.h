@@ -263,10 +263,15 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *               time on the server clock ("serve_now"), from which the latency
  *               is measured.
  *   "serve_step" server, OUT n_queued, OUT n_active, OUT n_completed
- *               Admit queued requests in arrival order within the limits,
- *               run one round of every active solve (requests that joined
- *               start, running ones continue), retire finished ones (result
- *               kept on the device until fetched).
+ *               Wait for the round the previous step launched and retire the
+ *               solves that finished in it (result kept on the device until
+ *               fetched); let the requests admitted meanwhile join; launch
+ *               the next round of every active solve (requests that joined
+ *               start, running ones continue) and admit queued requests in
+ *               arrival order within the limits while it runs.  Returns with
+ *               that round running, so the caller's submissions and fetches
+ *               overlap it; a solve is reported complete by the step after
+ *               the round in which it finished.
  *   "serve_result" server, ticket, [x: HOST or device double[nL]], OUT state,
  *               OUT iters, OUT rel_res, OUT latency_ms
  *               state 0 queued, 1 active, 2 done, 3 failed; when done, x

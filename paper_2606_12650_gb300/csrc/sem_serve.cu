@@ -69,6 +69,7 @@ struct Server {
     int64_t next_ticket = 1;
     int64_t completed = 0;
     bool changed = false;
+    bool in_flight = false;           // a round launched by the last step is running
     std::chrono::steady_clock::time_point t0;
 };
 
@@ -258,10 +259,67 @@ static int admit_queued(Server *S) {
     return SEM_OK;
 }
 
+// Retire the members that finished in the round just completed: results to
+// compact device buffers, problem memory released.
+static int retire(Server *S, const std::vector<int> &done) {
+    if (done.empty()) return SEM_OK;
+    const double t = serve_now(S);
+    // results of the finished members only
+    std::vector<int64_t> its(done.size());
+    std::vector<double> res(done.size());
+    int rc = batch_results_of(S->B, done, its.data(), res.data());
+    if (rc != SEM_OK) return rc;
+    std::vector<uint8_t> gone(S->active.size(), 0);
+    for (size_t j = 0; j < done.size(); ++j) {
+        const int k = done[j];
+        ServeReq *q = S->active[k];
+        q->x_dev = static_cast<double *>(dev_alloc(sizeof(double) * q->nL));
+        if (!q->x_dev) return SEM_ENOMEM;
+        rc = cuda_check(cudaMemcpyAsync(q->x_dev, q->P->x, sizeof(double) * q->nL, cudaMemcpyDeviceToDevice,
+                                        stream()), "serve: result");
+        if (rc != SEM_OK) return rc;
+        q->iters = its[j];
+        q->res = res[j];
+        q->t_done = t;
+        gone[k] = 1;
+    }
+    rc = cuda_check(cudaStreamSynchronize(stream()), "serve: sync");
+    if (rc != SEM_OK) return rc;
+    std::vector<ServeReq *> keep;
+    for (size_t k = 0; k < S->active.size(); ++k) {
+        ServeReq *q = S->active[k];
+        if (gone[k]) {
+            release_active(q);   // q->bytes stay counted until the result is fetched
+            q->state = 2;
+            ++S->completed;
+            S->finished.push_back(q->ticket);
+        } else {
+            keep.push_back(q);
+        }
+    }
+    S->active.swap(keep);
+    S->changed = true;
+    return SEM_OK;
+}
+
+// One step.  The step returns with the next round running, so that the
+// caller's own work (submitting, fetching results) overlaps it:
+// (1) wait for the round the previous step launched and retire the solves
+//     that finished in it;
+// (2) requests admitted meanwhile join (with nothing running, admission runs
+//     here first);
+// (3) the membership goes to the batch engine;
+// (4) the next round is launched, and queued requests are admitted on the
+//     admission stream while it runs.
 int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_completed) {
     int rc = SEM_OK;
-    // (1) requests admitted during the previous step join; with nothing
-    // running (a first step, or an idle server) admission runs here
+    if (S->in_flight) {
+        std::vector<int> done;
+        S->in_flight = false;
+        rc = batch_round_finish(S->B, &done);
+        if (rc == SEM_OK) rc = retire(S, done);
+        if (rc != SEM_OK) return rc;
+    }
     if (S->active.empty() && S->pending.empty()) {
         rc = admit_queued(S);
         if (rc != SEM_OK) return rc;
@@ -304,56 +362,13 @@ int serve_step(Server *S, int64_t *n_queued, int64_t *n_active, int64_t *n_compl
         for (ServeReq *q : S->active) q->fresh = false;
         S->changed = false;
     }
-    // (2) launch one round for every active solve; (3) admit meanwhile
-    const bool running = !S->active.empty();
-    if (running) {
+    if (!S->active.empty()) {
         rc = batch_round_launch(S->B);
         if (rc != SEM_OK) return rc;
+        S->in_flight = true;
     }
-    const int rc_admit = admit_queued(S);
-    // (4) wait for the round, retire the finished solves
-    std::vector<int> done;
-    if (running) rc = batch_round_finish(S->B, &done);
+    rc = admit_queued(S);
     if (rc != SEM_OK) return rc;
-    if (rc_admit != SEM_OK) return rc_admit;
-    if (!done.empty()) {
-        const double t = serve_now(S);
-        // results of the finished members only
-        std::vector<int64_t> its(done.size());
-        std::vector<double> res(done.size());
-        rc = batch_results_of(S->B, done, its.data(), res.data());
-        if (rc != SEM_OK) return rc;
-        std::vector<uint8_t> gone(S->active.size(), 0);
-        for (size_t j = 0; j < done.size(); ++j) {
-            const int k = done[j];
-            ServeReq *q = S->active[k];
-            q->x_dev = static_cast<double *>(dev_alloc(sizeof(double) * q->nL));
-            if (!q->x_dev) return SEM_ENOMEM;
-            rc = cuda_check(cudaMemcpyAsync(q->x_dev, q->P->x, sizeof(double) * q->nL, cudaMemcpyDeviceToDevice,
-                                            stream()), "serve: result");
-            if (rc != SEM_OK) return rc;
-            q->iters = its[j];
-            q->res = res[j];
-            q->t_done = t;
-            gone[k] = 1;
-        }
-        rc = cuda_check(cudaStreamSynchronize(stream()), "serve: sync");
-        if (rc != SEM_OK) return rc;
-        std::vector<ServeReq *> keep;
-        for (size_t k = 0; k < S->active.size(); ++k) {
-            ServeReq *q = S->active[k];
-            if (gone[k]) {
-                release_active(q);   // q->bytes stay counted until the result is fetched
-                q->state = 2;
-                ++S->completed;
-                S->finished.push_back(q->ticket);
-            } else {
-                keep.push_back(q);
-            }
-        }
-        S->active.swap(keep);
-        S->changed = true;
-    }
     *n_queued = int64_t(S->queue.size());
     *n_active = int64_t(S->active.size() + S->pending.size());
     *n_completed = S->completed;

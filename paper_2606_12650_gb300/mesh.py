@@ -141,7 +141,7 @@ class Server:
     """Continuous-batching solve server (one sem.run call per method)."""
 
     def __init__(self, capacity: int = 256, budget_gb: float = 40.0, mode: int = 1, tol: float = 1e-8,
-                 inner_tol: float = 1e-3, K: int = 8, maxit: int = 100000):
+                 inner_tol: float = 1e-3, K: int = 16, maxit: int = 100000):
         h = sem.OutInt()
         sem.run("serve_open", int(capacity), float(budget_gb), int(mode), float(tol), float(inner_tol),
                 int(K), int(maxit), h)

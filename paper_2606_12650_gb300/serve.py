@@ -66,7 +66,7 @@ def run_stream(server: Server, requests: list[dict], arrivals, collect_x: bool =
 
 
 def sweep(rates, count: int, seed: int, mode: int = 1, budget_gb: float = 40.0, capacity: int = 512,
-          K: int = 8, tol: float = 1e-8) -> list[dict]:
+          K: int = 16, tol: float = 1e-8) -> list[dict]:
     """p50 / p99 latency and throughput for each arrival rate (req/s)."""
     rows = []
     for q, rate in enumerate(rates):
