@@ -123,6 +123,8 @@ struct Batch {
     int ord_body[kOrders];          // operator body per order (kBodyNone: no member of that order)
     int ord_count[kOrders];         // operator items per order in the device list now
     int ord_vcount[kOrders];        // vector items per order in the device list now
+    int ord_res[kOrders] = {};      // resident CTAs of the order's operator and update kernels
+    int ord_vres[kOrders] = {};
     std::vector<uint8_t> gone;
     int cap_probs = 0, cap_ax = 0, cap_vec = 0;
     BatchProb *d_probs = nullptr;
@@ -670,36 +672,39 @@ struct BaxLaunch {
 // Dispatch on the order and body (prepare only, or launch for `count`
 // items).  The double-word body exists for FP64 CG batches only.
 template <typename T, typename GT, int MODE, int NQ>
-static int bax_order(Batch *B, int body, int count, bool launch) {
-    int res = 0;
+static int bax_order(Batch *B, int body, int count, bool launch, int *res) {
+    int r = 0;
+    if (!res) res = &r;
     switch (body) {
         case kBodyColumns:
             return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyColumns>::launch(B, count)
-                          : BaxLaunch<T, GT, MODE, NQ, kBodyColumns>::resident(&res);
+                          : BaxLaunch<T, GT, MODE, NQ, kBodyColumns>::resident(res);
         case kBodyLines:
             return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyLines>::launch(B, count)
-                          : BaxLaunch<T, GT, MODE, NQ, kBodyLines>::resident(&res);
+                          : BaxLaunch<T, GT, MODE, NQ, kBodyLines>::resident(res);
         case kBodyDW:
             if constexpr (MODE == 0)
                 return launch ? BaxLaunch<T, GT, MODE, NQ, kBodyDW>::launch(B, count)
-                              : BaxLaunch<T, GT, MODE, NQ, kBodyDW>::resident(&res);
+                              : BaxLaunch<T, GT, MODE, NQ, kBodyDW>::resident(res);
             [[fallthrough]];
         default: return set_error(SEM_EARG, "batch: no such operator body for this precision");
     }
 }
 
+// launch: launch order nq's kernel over `count` items; otherwise prepare it
+// and report its resident CTAs in *res.
 template <typename T, typename GT, int MODE>
-static int bax(Batch *B, int nq, int body, int count, bool launch) {
+static int bax(Batch *B, int nq, int body, int count, bool launch, int *res = nullptr) {
     switch (nq) {
-        case 2: return bax_order<T, GT, MODE, 2>(B, body, count, launch);
-        case 3: return bax_order<T, GT, MODE, 3>(B, body, count, launch);
-        case 4: return bax_order<T, GT, MODE, 4>(B, body, count, launch);
-        case 5: return bax_order<T, GT, MODE, 5>(B, body, count, launch);
-        case 6: return bax_order<T, GT, MODE, 6>(B, body, count, launch);
-        case 7: return bax_order<T, GT, MODE, 7>(B, body, count, launch);
-        case 8: return bax_order<T, GT, MODE, 8>(B, body, count, launch);
-        case 9: return bax_order<T, GT, MODE, 9>(B, body, count, launch);
-        case 10: return bax_order<T, GT, MODE, 10>(B, body, count, launch);
+        case 2: return bax_order<T, GT, MODE, 2>(B, body, count, launch, res);
+        case 3: return bax_order<T, GT, MODE, 3>(B, body, count, launch, res);
+        case 4: return bax_order<T, GT, MODE, 4>(B, body, count, launch, res);
+        case 5: return bax_order<T, GT, MODE, 5>(B, body, count, launch, res);
+        case 6: return bax_order<T, GT, MODE, 6>(B, body, count, launch, res);
+        case 7: return bax_order<T, GT, MODE, 7>(B, body, count, launch, res);
+        case 8: return bax_order<T, GT, MODE, 8>(B, body, count, launch, res);
+        case 9: return bax_order<T, GT, MODE, 9>(B, body, count, launch, res);
+        case 10: return bax_order<T, GT, MODE, 10>(B, body, count, launch, res);
         default: return set_error(SEM_EARG, "batch: unsupported order");
     }
 }
@@ -763,11 +768,12 @@ struct UpdLaunch {
 };
 
 template <int MODE>
-static int upd(Batch *B, int nq, int count, bool launch) {
-    int res = 0;
+static int upd(Batch *B, int nq, int count, bool launch, int *res = nullptr) {
+    int r = 0;
+    if (!res) res = &r;
     switch (nq) {
 #define SEM_UPD(Q) \
-    case Q: return launch ? UpdLaunch<MODE, Q>::launch(B, count) : UpdLaunch<MODE, Q>::resident(&res);
+    case Q: return launch ? UpdLaunch<MODE, Q>::launch(B, count) : UpdLaunch<MODE, Q>::resident(res);
         SEM_UPD(2) SEM_UPD(3) SEM_UPD(4) SEM_UPD(5) SEM_UPD(6) SEM_UPD(7) SEM_UPD(8) SEM_UPD(9) SEM_UPD(10)
 #undef SEM_UPD
         default: return set_error(SEM_EARG, "batch: unsupported order");
@@ -793,13 +799,13 @@ static int prepare_bax(Batch *B) {
         if (body == kBodyNone) continue;
         int rc;
         if (B->mode == 0) {
-            rc = bax<double, double, 0>(B, o + 2, body, 0, false);
-            if (rc == SEM_OK) rc = upd<kVecUpdate64>(B, o + 2, 0, false);
+            rc = bax<double, double, 0>(B, o + 2, body, 0, false, &B->ord_res[o]);
+            if (rc == SEM_OK) rc = upd<kVecUpdate64>(B, o + 2, 0, false, &B->ord_vres[o]);
         } else {
-            rc = B->mode == 1 ? bax<float, __nv_bfloat16, 2>(B, o + 2, body, 0, false)
-                              : bax<float, float, 2>(B, o + 2, body, 0, false);
+            rc = B->mode == 1 ? bax<float, __nv_bfloat16, 2>(B, o + 2, body, 0, false, &B->ord_res[o])
+                              : bax<float, float, 2>(B, o + 2, body, 0, false, &B->ord_res[o]);
             if (rc == SEM_OK) rc = bax<double, double, 1>(B, o + 2, body, 0, false);
-            if (rc == SEM_OK) rc = upd<kVecUpdate32>(B, o + 2, 0, false);
+            if (rc == SEM_OK) rc = upd<kVecUpdate32>(B, o + 2, 0, false, &B->ord_vres[o]);
         }
         if (rc != SEM_OK) return rc;
     }
@@ -919,12 +925,14 @@ static int upload_order_ranges(Batch *B, const int *ord_first) {
 }
 
 // What a captured round's launches depend on: per order, its operator body
-// and the power-of-two ceilings of its item counts (0: no launches).
+// and the two launches' grids (0: no launches).  A grid is the resident CTAs
+// or, for fewer items, their power-of-two ceiling, so item counts can change
+// a lot at large sizes without a new capture.
 static void order_signature(const Batch *B, int *out) {
     for (int o = 0; o < kOrders; ++o) {
         const bool on = B->ord_body[o] != kBodyNone;
-        out[o] = on ? 4 * items_grid(1 << 30, B->ord_count[o]) + B->ord_body[o] + 1 : 0;
-        out[kOrders + o] = on ? items_grid(1 << 30, B->ord_vcount[o]) : 0;
+        out[o] = on ? 4 * items_grid(B->ord_res[o], B->ord_count[o]) + B->ord_body[o] + 1 : 0;
+        out[kOrders + o] = on ? items_grid(B->ord_vres[o], B->ord_vcount[o]) : 0;
     }
 }
 
