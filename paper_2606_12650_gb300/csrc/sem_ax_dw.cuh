@@ -208,35 +208,36 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
     dwf *SU = reinterpret_cast<dwf *>(CG ? regA : regB) + eb * NPP;
     dwf *SV = reinterpret_cast<dwf *>(regC) + eb * NPP;
 
-    // ---- (1) gradient lines
+    // ---- (1) gradient lines.  FOLD: the r and s lines share one copy of the
+    // (long, fully unrolled) double-word contraction -- a two-pass loop over
+    // (first node, stride, rotation, destination) -- since the unrolled body
+    // outgrows the instruction cache (no-instruction stalls; N+1 = 8:
+    // 373 -> 358 us).  Not at N+1 = 9, where the loop's addressing takes 92
+    // registers instead of 64.
+    constexpr bool FOLD = NQ != 9;
     dwf ut[NQ];
     if (act) {
         dwf u[NQ], yl[NQ];
-        if (ROT) {
-            const int R = (ab / RPB) & (NQ - 1);
+        auto rs_line = [&](int d) {
+            const int q0 = d ? cq : rq, st = d ? NQ : 1;
+            const int R = ROT ? (d ? (b & (NQ - 1)) : ((ab / RPB) & (NQ - 1))) : 0;
 #pragma unroll
-            for (int l = 0; l < NQ; ++l) u[l] = SX[rq + ((l + R) & (NQ - 1))];
-            rotate_right<NQ, dwf>(u, R);
+            for (int l = 0; l < NQ; ++l) u[l] = SX[q0 + (ROT ? ((l + R) & (NQ - 1)) : l) * st];
+            if (ROT) rotate_right<NQ, dwf>(u, R);
+            eo_apply_dw<NQ>(u, yl, cd);
+            dwf *dst = d ? SV + cp : SU + rp;
+            const int ds = d ? P1 : 1;
+#pragma unroll
+            for (int l = 0; l < NQ; ++l) dst[l * ds] = yl[l];
+        };
+        if constexpr (FOLD) {
+#pragma unroll 1
+            for (int d = 0; d < 2; ++d) rs_line(d);
         } else {
-#pragma unroll
-            for (int l = 0; l < NQ; ++l) u[l] = SX[rq + l];
+            rs_line(0);
+            rs_line(1);
         }
-        eo_apply_dw<NQ>(u, yl, cd);
-#pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rp + l] = yl[l];
-        if (ROT) {
-            const int R = b & (NQ - 1);
-#pragma unroll
-            for (int l = 0; l < NQ; ++l) u[l] = SX[cq + ((l + R) & (NQ - 1)) * NQ];
-            rotate_right<NQ, dwf>(u, R);
-        } else {
-#pragma unroll
-            for (int l = 0; l < NQ; ++l) u[l] = SX[cq + l * NQ];
-        }
-        eo_apply_dw<NQ>(u, yl, cd);
-#pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = yl[l];
-        eo_apply_dw<NQ>(xk, ut, cd);
+        eo_apply_dw<NQ>(xk, ut, cd);   // the t line, from the registers of the prologue
     }
     __syncthreads();
 
@@ -256,21 +257,29 @@ __device__ __forceinline__ bool lines_group_dw(const double *x, double *y, doubl
     }
     __syncthreads();
 
-    // ---- (3) divergence lines (in place: each line has one owner)
+    // ---- (3) divergence lines (in place: each line has one owner); FOLD as
+    // in phase 1
     dwf yt[NQ];
     if (act) {
         dwf u[NQ], yl[NQ];
+        auto rs_line = [&](int d) {
+            dwf *line = d ? SV + cp : SU + rp;
+            const int ls = d ? P1 : 1;
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SU[rp + l];
-        eo_apply_dw<NQ>(u, yl, ct);
+            for (int l = 0; l < NQ; ++l) u[l] = line[l * ls];
+            eo_apply_dw<NQ>(u, yl, ct);
 #pragma unroll
-        for (int l = 0; l < NQ; ++l) SU[rp + l] = yl[l];
-#pragma unroll
-        for (int l = 0; l < NQ; ++l) u[l] = SV[cp + l * P1];
-        eo_apply_dw<NQ>(u, yl, ct);
-#pragma unroll
-        for (int l = 0; l < NQ; ++l) SV[cp + l * P1] = yl[l];
-        eo_apply_dw<NQ>(wt, yt, ct);
+            for (int l = 0; l < NQ; ++l) line[l * ls] = yl[l];
+        };
+        if constexpr (FOLD) {
+#pragma unroll 1
+            for (int d = 0; d < 2; ++d) rs_line(d);
+        } else {
+            rs_line(0);
+            rs_line(1);
+        }
+        eo_apply_dw<NQ>(wt, yt, ct);   // the t line (registers), out of the loop, whose
+                                       // iterations would otherwise hold wt and yt live together
     }
     __syncthreads();
 
