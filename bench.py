@@ -740,7 +740,7 @@ def run_batched(a, job, rank, stream, sem, torch):
     setup_s = time.perf_counter() - t0
     gdof_per_iter = np.array([m.E * m.N ** 3 for m in meshes], dtype=np.float64)
     out = {"workload": f"{len(meshes)} problems, E log-uniform [8, 4096] (near-cubic boxes), N in {{3,5,7,9}}, "
-                       f"jitter 5%, random RHS; tol {a.tol:g}; every CG phase one persistent launch",
+                       f"jitter 5%, random RHS; tol {a.tol:g}; per order one persistent launch per CG phase, the orders in parallel",
            "problems": len(meshes), "local_dofs_total": int(B.nL_total), "tuned_per_order": tuned,
            "E_total": int(sum(m.E for m in meshes)), "setup_s": setup_s}
     for mode, name in ((0, "fp64"), (1, "mixed_bf16")):

@@ -242,9 +242,10 @@ int sem_update(void *host, size_t start, size_t end, size_t elem_size, int op);
  *   "batch_solve" batch, b_all, x_all, tol, maxit, mode, inner_tol, max_outer,
  *               OUT total_iters, OUT max_rel_res, [iters HOST int64[n]],
  *               [rel_res HOST double[n]]
- *               Solve every problem of the batch at once: each CG phase is one
- *               persistent launch over all problems (dynamic work list, switch
- *               on N), replayed from a CUDA graph.  mode 0: FP64 CG to tol;
+ *               Solve every problem of the batch at once: per order present,
+ *               each CG phase is one persistent launch over that order's
+ *               problems (dynamic work list), the orders' iterations parallel
+ *               chains of one CUDA graph.  mode 0: FP64 CG to tol;
  *               mode 1 / 2: mixed-precision refinement (as "cg_mixed") with G
  *               in BF16 / FP32.  A problem's iterates do not depend on the
  *               other problems in the batch.  iters: CG iterations (mode 0) or
