@@ -108,7 +108,8 @@ class Mesh:
 
 
 class Batch:
-    """Problems solved together: every CG phase is one persistent launch."""
+    """Problems solved together: per order present, each CG phase is one
+    persistent launch over that order's problems (sem.h, "batch_solve")."""
 
     def __init__(self, meshes):
         self.meshes = list(meshes)
