@@ -1,5 +1,5 @@
-"""Batched solves: many problems of different sizes and orders in one
-persistent launch per CG phase.
+"""Batched solves: many problems of different sizes and orders, per order
+one persistent launch per CG phase, the orders' chains in parallel.
 
 Checks: every problem of a mixed batch reaches its tolerance with the
 oracle's own operator (true residual within 1.5x of tol, the FP64 slack used
@@ -120,6 +120,32 @@ def test_batch_invariance_alone_vs_in_the_mix(semlib, oracle_mod, mode):
     sub = [meshes[3], meshes[0], meshes[8]]
     _, _, xs_sub = _solve(sub, [bs[3], bs[0], bs[8]], 1e-8, mode)
     np.testing.assert_array_equal(xs_sub[0], xs_all[3])
+    for m in meshes:
+        m.free()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_every_order_alone_and_mixed(semlib, oracle_mod, mode):
+    """Two problems of each order N = 1..9 (18 problems, nine per-order
+    kernel chains in one round): each reaches its tolerance under the
+    oracle's operator, and the first problem of every order gives the same
+    bits alone (batch of one) as in the full mix."""
+    specs = []
+    for N in range(1, 10):
+        specs.append((2, 2, 1, N))
+        specs.append((3, 2, 2, N) if N <= 6 else (2, 2, 2, N))
+    meshes, probs, bs = _build(oracle_mod, specs)
+    tol = 1e-9
+    its, res, xs = _solve(meshes, bs, tol, mode)
+    for k, (P, b, x) in enumerate(zip(probs, bs, xs)):
+        if not np.any(b):
+            continue
+        assert res[k] <= tol, (k, specs[k], res[k])
+        assert P.true_residual(b, x) <= 1.5 * tol, (k, specs[k])
+    for k in range(0, len(specs), 2):
+        its1, res1, xs1 = _solve([meshes[k]], [bs[k]], tol, mode)
+        assert its1[0] == its[k], specs[k]
+        np.testing.assert_array_equal(xs1[0], xs[k])
     for m in meshes:
         m.free()
 
