@@ -568,6 +568,9 @@ def summarize(value, ms_fp64, roofline, mixed, batched, served, pcg, vs_oracle):
     if batched:
         s["batched_solves_per_s"] = {"fp64": batched["fp64"]["solves_per_s"],
                                      "mixed": batched["mixed_bf16"]["solves_per_s"]}
+        if "roofline" in batched["fp64"]:
+            s["batched_hbm_frac"] = {"fp64": batched["fp64"]["roofline"]["frac"],
+                                     "mixed": batched["mixed_bf16"]["roofline"]["frac"]}
     if served:
         s["served"] = [{"rate": r["rate_req_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                         "solves_per_s": r["solves_per_s"]} for r in served["rates"]]
@@ -739,6 +742,12 @@ def run_batched(a, job, rank, stream, sem, torch):
     x_all = torch.empty_like(b_all)
     setup_s = time.perf_counter() - t0
     gdof_per_iter = np.array([m.E * m.N ** 3 for m in meshes], dtype=np.float64)
+    nL = np.array([m.nL for m in meshes], dtype=np.float64)
+    # algorithmic bytes per local node and CG iteration: FP64 -- operator r, p
+    # in, p, w out, 48 B of factors (80), update x, r, p, w in, x, r out (48);
+    # mixed -- FP32 operator with BF16 factors (28), FP32 update (24)
+    bytes_per_node_iter = {"fp64": 128.0, "mixed_bf16": 52.0}
+    hbm, hbm_how = hbm_peak()
     out = {"workload": f"{len(meshes)} problems, E log-uniform [8, 4096] (near-cubic boxes), N in {{3,5,7,9}}, "
                        f"jitter 5%, random RHS; tol {a.tol:g}; per order one persistent launch per CG phase, the orders in parallel",
            "problems": len(meshes), "local_dofs_total": int(B.nL_total), "tuned_per_order": tuned,
@@ -755,6 +764,13 @@ def run_batched(a, job, rank, stream, sem, torch):
         ms, dofs = job.aggregate(e0.elapsed_time(e1), float((gdof_per_iter * its).sum()))
         out[name] = {"ms": ms, "gdofs": dofs / (ms * 1e-3) / 1e9, "solves_per_s": 1e3 * len(meshes) * world / ms,
                      "iters_total": int(its.sum()), "iters_max": int(its.max()), "max_rel_res": float(res.max())}
+        # the roofline summed over the problems: HBM time of each problem's
+        # own iterations' algorithmic bytes (inner iterations for mixed; the
+        # refinement steps' few FP64 passes not counted), against the batch time
+        hbm_ms = float((its * nL).sum()) * bytes_per_node_iter[name] / (hbm * 1e9) * 1e3   # per GPU (replicas)
+        out[name]["roofline"] = {"bound": "hbm", "alg_bytes_per_node_iter": bytes_per_node_iter[name],
+                                 "hbm_time_ms": hbm_ms, "frac": hbm_ms / ms, "peak_gbs": hbm,
+                                 "peak_source": hbm_how}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed_bf16"]["ms"]
     B.free()
     for (k, N), (v, e, _) in saved.items():      # the later legs use the table tuned on the main problem
